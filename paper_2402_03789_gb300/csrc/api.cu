@@ -1,0 +1,814 @@
+// C ABI, model construction and the evaluation schedule.
+//
+// One evaluation (paper Figure 2a: forward path blue, reverse path orange):
+//   neighbour build -> embedding -> per block [linear_1 + self-connection,
+//   convolution, linear_2, gate] -> readout and FP64 energy -> reverse:
+//   per block from the last [gate adjoint, linear_2^T, convolution adjoint
+//   (edge gradients dE/dd accumulated over blocks, Eq. 5), linear_1^T and
+//   self-connection^T] -> F_v = sum_w (F_vw - F_wv) (Eq. 6) and the virial.
+#include "internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+
+namespace sn {
+
+thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+int num_sms(int device) {
+    static int cached[64] = {0};
+    if (device < 0 || device >= 64) return 132;
+    if (!cached[device]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0) v = 132;
+        cached[device] = v;
+    }
+    return cached[device];
+}
+
+// ---------------------------------------------------------------- layer specs
+struct PathH { int l1, l2, l3, mul; };
+
+static bool config_valid(const sevennet_model_config* c, std::string* why) {
+    auto fail = [&](const char* m) { if (why) *why = m; return false; };
+    if (!c) return fail("config is NULL");
+    if (c->n_species < 1) return fail("n_species must be >= 1");
+    if (c->n_layers < 1 || c->n_layers > 16) return fail("n_layers must be in [1, 16]");
+    if (c->lmax < 1 || c->lmax > MAX_LMAX) return fail("lmax must be 1 or 2");
+    for (int l = 0; l <= c->lmax; ++l)
+        if (c->mul[l] < 32 || c->mul[l] % 32 || c->mul[l] > 256) return fail("mul[l] must be a multiple of 32 in [32, 256]");
+    if (!(c->r_cut > 0) || !std::isfinite(c->r_cut)) return fail("r_cut must be positive");
+    if (c->n_basis < 1 || c->n_basis > MAX_NB) return fail("n_basis must be in [1, 16]");
+    if (c->poly_p < 1 || c->poly_p > 32) return fail("poly_p must be in [1, 32]");
+    if (c->mlp_hidden != 32 && c->mlp_hidden != 64) return fail("mlp_hidden must be 32 or 64");
+    if (!(c->avg_num_neigh > 0)) return fail("avg_num_neigh must be positive");
+    if (c->readout_hidden < 1 || c->readout_hidden > 1024) return fail("readout_hidden out of range");
+    return true;
+}
+
+static void block_irreps(const sevennet_model_config* c, int t, int in_mul[3], int y_mul[3],
+                         int out_mul[3], std::vector<PathH>& paths, int msg_mul[3], bool* last) {
+    const int T = c->n_layers, lmax = c->lmax;
+    *last = (t == T - 1);
+    for (int l = 0; l < 3; ++l) in_mul[l] = y_mul[l] = out_mul[l] = msg_mul[l] = 0;
+    if (t == 0) in_mul[0] = c->mul[0];
+    else for (int l = 0; l <= lmax; ++l) in_mul[l] = c->mul[l];
+    paths.clear();
+    for (int l1 = 0; l1 <= 2; ++l1) {
+        if (!in_mul[l1]) continue;
+        for (int l2 = 0; l2 <= lmax; ++l2)
+            for (int l3 = std::abs(l1 - l2); l3 <= std::min(l1 + l2, lmax); ++l3) {
+                if (*last && l3 != 0) continue;
+                paths.push_back({l1, l2, l3, in_mul[l1]});
+                msg_mul[l3] += in_mul[l1];
+            }
+    }
+    if (*last) {
+        y_mul[0] = c->mul[0];
+        out_mul[0] = c->mul[0];
+    } else {
+        y_mul[0] = c->mul[0];
+        for (int l = 1; l <= lmax; ++l) { y_mul[0] += c->mul[l]; y_mul[l] = c->mul[l]; out_mul[l] = c->mul[l]; }
+        out_mul[0] = c->mul[0];
+    }
+}
+
+static void offsets(const int mul[3], int off[3], int* dim) {
+    int o = 0;
+    for (int l = 0; l < 3; ++l) { off[l] = o; o += (2 * l + 1) * mul[l]; }
+    *dim = o;
+}
+
+struct WEntry { std::string name; int rows, cols; int64_t off; };
+
+static std::vector<WEntry> weight_entries(const sevennet_model_config* c) {
+    std::vector<WEntry> e;
+    int64_t off = 0;
+    auto add = [&](const std::string& n, int r, int k) { e.push_back({n, r, k, off}); off += (int64_t)r * k; };
+    add("embed", c->n_species, c->mul[0]);
+    const int H = c->mlp_hidden;
+    for (int t = 0; t < c->n_layers; ++t) {
+        int in_mul[3], y_mul[3], out_mul[3], msg_mul[3];
+        std::vector<PathH> paths;
+        bool last;
+        block_irreps(c, t, in_mul, y_mul, out_mul, paths, msg_mul, &last);
+        const std::string p = "L" + std::to_string(t) + ".";
+        for (int l = 0; l < 3; ++l)
+            if (y_mul[l] && in_mul[l]) add(p + "sc." + std::to_string(l), in_mul[l], y_mul[l]);
+        for (int l = 0; l < 3; ++l)
+            if (in_mul[l]) add(p + "lin1." + std::to_string(l), in_mul[l], in_mul[l]);
+        int W = 0;
+        for (auto& q : paths) W += q.mul;
+        add(p + "mlp0", c->n_basis, H);
+        add(p + "mlp1", H, H);
+        add(p + "mlp2", H, W);
+        for (int l = 0; l < 3; ++l)
+            if (y_mul[l] && msg_mul[l]) add(p + "lin2." + std::to_string(l), msg_mul[l], y_mul[l]);
+    }
+    add("readout0", c->mul[0], c->readout_hidden);
+    add("readout1", c->readout_hidden, 1);
+    return e;
+}
+
+// ---------------------------------------------------------------- device upload
+template <typename T>
+static sevennet_status dev_upload(sevennet_model* M, const std::vector<T>& h, T** out) {
+    *out = nullptr;
+    if (h.empty()) return SEVENNET_OK;
+    void* p = nullptr;
+    if (cudaMalloc(&p, h.size() * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of %zu bytes failed", h.size() * sizeof(T));
+        return SEVENNET_ENOMEM;
+    }
+    M->allocations.push_back(p);
+    SN_CUDA(cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *out = static_cast<T*>(p);
+    return SEVENNET_OK;
+}
+
+static std::vector<float> scaled(const double* w, int rows, int cols, double s, bool transpose) {
+    std::vector<float> o((size_t)rows * cols);
+    for (int i = 0; i < rows; ++i)
+        for (int j = 0; j < cols; ++j) {
+            const float v = (float)(w[(size_t)i * cols + j] * s);
+            if (transpose) o[(size_t)j * rows + i] = v; else o[(size_t)i * cols + j] = v;
+        }
+    return o;
+}
+
+static std::vector<__nv_bfloat16> to_bf16(const std::vector<float>& f) {
+    std::vector<__nv_bfloat16> o(f.size());
+    for (size_t i = 0; i < f.size(); ++i) o[i] = __float2bfloat16_rn(f[i]);
+    return o;
+}
+
+static sevennet_status upload_linear(sevennet_model* M, const double* w, int rows, int cols, double s,
+                                     float** W, float** WT, __nv_bfloat16** Wh, __nv_bfloat16** WTh) {
+    auto a = scaled(w, rows, cols, s, false);
+    auto b = scaled(w, rows, cols, s, true);
+    SN_TRY(dev_upload(M, a, W));
+    SN_TRY(dev_upload(M, b, WT));
+    SN_TRY(dev_upload(M, to_bf16(b), Wh));     // [cols][rows]: N-major B operand of out = in @ W
+    SN_TRY(dev_upload(M, to_bf16(a), WTh));    // [rows][cols]: N-major B operand of gin = gout @ W^T
+    return SEVENNET_OK;
+}
+
+// Balanced assignment of 32-channel path groups to warps (longest first).
+static bool assign_slots(ConvDesc& D) {
+    struct G { int p, ub, cost; };
+    std::vector<G> gs;
+    for (int p = 0; p < D.n_paths; ++p) {
+        const PathDesc& P = D.paths[p];
+        const int n1 = 2 * P.l1 + 1, n3 = 2 * P.l3 + 1;
+        for (int ub = 0; ub < P.mul / 32; ++ub) gs.push_back({p, ub, n1 * n3 + n1 + 3});
+    }
+    std::stable_sort(gs.begin(), gs.end(), [](const G& a, const G& b) { return a.cost > b.cost; });
+    int load[CONV_WARPS] = {0};
+    for (int w = 0; w < CONV_WARPS; ++w) D.n_slots[w] = 0;
+    for (const G& g : gs) {
+        int best = -1;
+        for (int w = 0; w < CONV_WARPS; ++w)
+            if (D.n_slots[w] < MAX_SLOTS && (best < 0 || load[w] < load[best])) best = w;
+        if (best < 0) return false;
+        D.slot_group[best][D.n_slots[best]++] = (int16_t)((g.p << 8) | g.ub);
+        load[best] += g.cost;
+    }
+    return true;
+}
+
+}  // namespace sn
+
+using namespace sn;
+
+// ---------------------------------------------------------------- workspace
+namespace sn {
+
+template <typename T>
+static sevennet_status ws_alloc(Workspace* ws, T** p, int64_t count) {
+    if (*p) {
+        cudaFree(*p);
+        ws->allocs.erase(std::remove(ws->allocs.begin(), ws->allocs.end(), (void*)*p), ws->allocs.end());
+        *p = nullptr;
+    }
+    if (count <= 0) count = 1;
+    void* q = nullptr;
+    if (cudaMalloc(&q, (size_t)count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of %lld bytes failed", (long long)(count * (int64_t)sizeof(T)));
+        return SEVENNET_ENOMEM;
+    }
+    ws->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return SEVENNET_OK;
+}
+
+sevennet_status ws_reserve(sevennet_model* M, Workspace* ws, int64_t n_atoms, int64_t n_edges,
+                           int64_t n_bins, int64_t n_structs, cudaStream_t st) {
+    SN_CUDA(cudaStreamSynchronize(st));
+    if (!ws->flags) {
+        SN_TRY(ws_alloc(ws, &ws->flags, 8));
+        void* hp = nullptr;
+        SN_CUDA(cudaMallocHost(&hp, 8 * sizeof(int)));
+        ws->flags_host = static_cast<int*>(hp);
+    }
+    if (n_atoms > ws->cap_atoms) {
+        const int64_t N = std::max<int64_t>(n_atoms, 16);
+        const int T = M->T;
+        SN_TRY(ws_alloc(ws, &ws->bin_of, N));
+        SN_TRY(ws_alloc(ws, &ws->perm, N));
+        SN_TRY(ws_alloc(ws, &ws->struct_of, N));
+        SN_TRY(ws_alloc(ws, &ws->pos_s, N * 3));
+        SN_TRY(ws_alloc(ws, &ws->frac_floor, N * 3));
+        SN_TRY(ws_alloc(ws, &ws->species_s, N));
+        SN_TRY(ws_alloc(ws, &ws->row_ptr, N + 1));
+        SN_TRY(ws_alloc(ws, &ws->row_cnt, N + 1));
+        SN_TRY(ws_alloc(ws, &ws->h, N * M->h_max));
+        SN_TRY(ws_alloc(ws, &ws->xs, (int64_t)T * N * M->x_max));
+        SN_TRY(ws_alloc(ws, &ws->ys, (int64_t)T * N * M->y_max));
+        SN_TRY(ws_alloc(ws, &ws->m, N * M->m_max));
+        SN_TRY(ws_alloc(ws, &ws->gy, N * M->y_max));
+        SN_TRY(ws_alloc(ws, &ws->gx, N * M->x_max));
+        SN_TRY(ws_alloc(ws, &ws->gh, N * M->h_max));
+        SN_TRY(ws_alloc(ws, &ws->e_atom, N));
+        SN_TRY(ws_alloc(ws, &ws->w_atom, N * 9));
+        SN_TRY(ws_alloc(ws, &ws->f_s, N * 3));
+        ws->cap_atoms = N;
+    }
+    if (n_edges > ws->cap_edges) {
+        const int64_t E = std::max<int64_t>(n_edges, 1024);
+        SN_CHECK(E < (1LL << 31) - 1, SEVENNET_EOVERFLOW, "edge count exceeds 2^31");
+        SN_TRY(ws_alloc(ws, &ws->dst, E));
+        SN_TRY(ws_alloc(ws, &ws->src, E));
+        SN_TRY(ws_alloc(ws, &ws->shift, E * 3));
+        SN_TRY(ws_alloc(ws, &ws->rev, E));
+        SN_TRY(ws_alloc(ws, &ws->geom, E));
+        SN_TRY(ws_alloc(ws, &ws->gd, E * 3));
+        ws->cap_edges = E;
+    }
+    if (n_bins + 1 > ws->cap_bins) {
+        const int64_t B = std::max<int64_t>(n_bins + 1, 64);
+        SN_TRY(ws_alloc(ws, &ws->bin_count, B + 1));
+        SN_TRY(ws_alloc(ws, &ws->bin_start, B + 1));
+        SN_TRY(ws_alloc(ws, &ws->bin_fill, B + 1));
+        ws->cap_bins = B;
+    }
+    if (n_structs > ws->cap_structs) {
+        const int64_t S = std::max<int64_t>(n_structs, 4);
+        SN_TRY(ws_alloc(ws, &ws->cells, S * 9));
+        SN_TRY(ws_alloc(ws, &ws->inv_cells, S * 9));
+        SN_TRY(ws_alloc(ws, &ws->sdesc, S * 16));
+        SN_TRY(ws_alloc(ws, &ws->atom_off, S + 1));
+        ws->cap_structs = S;
+    }
+    return SEVENNET_OK;
+}
+
+void ws_free(Workspace* ws) {
+    if (!ws) return;
+    for (void* p : ws->allocs) cudaFree(p);
+    ws->allocs.clear();
+    if (ws->flags_host) cudaFreeHost(ws->flags_host);
+    delete ws;
+}
+
+// ---------------------------------------------------------------- evaluation
+sevennet_status run_model(sevennet_model* M, Workspace* ws, const BatchHost& b, int64_t E,
+                          sevennet_precision prec, double* energy_dev, double* forces_dev,
+                          double* virial_dev, cudaStream_t st) {
+    const int64_t N = b.atom_off[b.n_structs];
+    const int T = M->T;
+    const int mul0 = M->cfg.mul[0];
+    launch_embed(M->embed, ws->species_s, N, mul0, M->cfg.n_species, ws->h, st);
+    for (int t = 0; t < T; ++t) {
+        const LayerDev& L = M->layers[t];
+        float* x = ws->xs + (size_t)t * N * M->x_max;
+        float* y = ws->ys + (size_t)t * N * M->y_max;
+        GemmBatch g{};
+        for (int l = 0; l < 3; ++l) {
+            if (!L.in_mul[l]) continue;
+            g.p[g.n++] = GemmProb{ws->h, L.lin1[l], L.lin1h[l], x, N, 2 * l + 1, L.in_mul[l], L.in_mul[l],
+                                  L.h_in_dim, L.in_off[l], L.x_dim, L.in_off[l], 0};
+            if (L.y_mul[l])
+                g.p[g.n++] = GemmProb{ws->h, L.sc[l], L.sch[l], y, N, 2 * l + 1, L.in_mul[l], L.y_mul[l],
+                                      L.h_in_dim, L.in_off[l], L.y_dim, L.y_off[l], 0};
+        }
+        launch_gemm(g, prec, st);
+        launch_conv_fwd(L, M->H, prec, N, E, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m, st);
+        GemmBatch g2{};
+        for (int l = 0; l < 3; ++l) {
+            if (!L.y_mul[l] || !L.msg_mul[l]) continue;
+            g2.p[g2.n++] = GemmProb{ws->m, L.lin2[l], L.lin2h[l], y, N, 2 * l + 1, L.msg_mul[l], L.y_mul[l],
+                                    L.m_dim, L.msg_off[l], L.y_dim, L.y_off[l], L.in_mul[l] ? 1 : 0};
+        }
+        launch_gemm(g2, prec, st);
+        launch_gate_fwd(L, mul0, M->cfg.mul, M->lmax, N, y, ws->h, st);
+    }
+    launch_readout(ws->h, M->layers[T - 1].h_out_dim, M->readout, M->shift_dev, ws->species_s, N, mul0,
+                   M->cfg.n_species, ws->e_atom, st);
+    // reverse path
+    if (E > 0) SN_CUDA(cudaMemsetAsync(ws->gd, 0, (size_t)E * 3 * sizeof(float), st));
+    for (int t = T - 1; t >= 0; --t) {
+        const LayerDev& L = M->layers[t];
+        float* x = ws->xs + (size_t)t * N * M->x_max;
+        float* y = ws->ys + (size_t)t * N * M->y_max;
+        launch_gate_bwd(L, mul0, M->cfg.mul, M->lmax, N, y, ws->gh, M->readout, ws->gy, st);
+        GemmBatch g{};
+        for (int l = 0; l < 3; ++l) {
+            if (!L.y_mul[l] || !L.msg_mul[l]) continue;
+            g.p[g.n++] = GemmProb{ws->gy, L.lin2T[l], L.lin2Th[l], ws->m, N, 2 * l + 1, L.y_mul[l], L.msg_mul[l],
+                                  L.y_dim, L.y_off[l], L.m_dim, L.msg_off[l], 0};
+        }
+        launch_gemm(g, prec, st);
+        SN_CUDA(cudaMemsetAsync(ws->gx, 0, (size_t)N * L.x_dim * sizeof(float), st));
+        launch_conv_bwd(L, M->H, prec, N, E, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m, ws->gx,
+                        ws->gd, st);
+        if (t == 0) break;
+        GemmBatch a{}, c{};
+        for (int l = 0; l < 3; ++l) {
+            if (!L.in_mul[l]) continue;
+            a.p[a.n++] = GemmProb{ws->gx, L.lin1T[l], L.lin1Th[l], ws->gh, N, 2 * l + 1, L.in_mul[l], L.in_mul[l],
+                                  L.x_dim, L.in_off[l], L.h_in_dim, L.in_off[l], 0};
+            if (L.y_mul[l])
+                c.p[c.n++] = GemmProb{ws->gy, L.scT[l], L.scTh[l], ws->gh, N, 2 * l + 1, L.y_mul[l], L.in_mul[l],
+                                      L.y_dim, L.y_off[l], L.h_in_dim, L.in_off[l], 1};
+        }
+        launch_gemm(a, prec, st);
+        launch_gemm(c, prec, st);
+    }
+    launch_forces(N, ws->row_ptr, ws->rev, ws->gd, ws->geom, ws->f_s, ws->w_atom, st);
+    launch_reduce_structs(b.n_structs, ws->atom_off, ws->e_atom, ws->w_atom, energy_dev, virial_dev, st);
+    launch_scatter_forces(N, ws->perm, ws->f_s, forces_dev, st);
+    SN_CUDA(cudaGetLastError());
+    return SEVENNET_OK;
+}
+
+}  // namespace sn
+
+// ======================================================================= C ABI
+extern "C" {
+
+const char* sevennet_last_error(void) { return sn::g_last_error.c_str(); }
+
+int64_t sevennet_n_params(const sevennet_model_config* cfg) {
+    std::string why;
+    if (!config_valid(cfg, &why)) {
+        set_error("%s", why.c_str());
+        return -1;
+    }
+    auto e = weight_entries(cfg);
+    return e.back().off + (int64_t)e.back().rows * e.back().cols;
+}
+
+sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const double* weights,
+                                      size_t n_weights, int device, sevennet_model** out) {
+    SN_CHECK(out, SEVENNET_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    SN_CHECK(config_valid(cfg, &why), SEVENNET_EINVAL, "%s", why.c_str());
+    const int64_t need = sevennet_n_params(cfg);
+    SN_CHECK(weights && (int64_t)n_weights == need, SEVENNET_EINVAL,
+             "weight vector has %zu entries, the model needs %lld", n_weights, (long long)need);
+    for (size_t i = 0; i < n_weights; ++i)
+        SN_CHECK(std::isfinite(weights[i]), SEVENNET_EINVAL, "weight %zu is not finite", i);
+    int ndev = 0;
+    SN_CUDA(cudaGetDeviceCount(&ndev));
+    SN_CHECK(device >= 0 && device < ndev, SEVENNET_EINVAL, "device %d out of range (%d devices)", device, ndev);
+    SN_CUDA(cudaSetDevice(device));
+    int major = 0, minor = 0;
+    SN_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device));
+    SN_CUDA(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device));
+    SN_CHECK(major == 10 && minor == 3, SEVENNET_EINVAL,
+             "device %d is sm_%d%d; this library is built for sm_103a only", device, major, minor);
+
+    auto* M = new sevennet_model();
+    M->device = device;
+    M->cfg = *cfg;
+    M->shift.assign(cfg->n_species, 0.0);
+    if (cfg->shift) for (int s = 0; s < cfg->n_species; ++s) M->shift[s] = cfg->shift[s];
+    M->cfg.shift = nullptr;
+    M->T = cfg->n_layers;
+    M->lmax = cfg->lmax;
+    M->H = cfg->mlp_hidden;
+    M->NB = cfg->n_basis;
+    auto fail = [&](sevennet_status s) { sevennet_destroy_model(M); return s; };
+
+    auto entries = weight_entries(cfg);
+    auto find = [&](const std::string& n) -> const WEntry* {
+        for (auto& e : entries) if (e.name == n) return &e;
+        return nullptr;
+    };
+    // embedding and readout
+    {
+        const WEntry* e = find("embed");
+        std::vector<float> t((size_t)e->rows * e->cols);
+        for (size_t i = 0; i < t.size(); ++i) t[i] = (float)weights[e->off + i];
+        sevennet_status s = dev_upload(M, t, &M->embed);
+        if (s) return fail(s);
+        const WEntry* r0 = find("readout0");
+        const WEntry* r1 = find("readout1");
+        const int hid = cfg->readout_hidden;
+        std::vector<float> c(cfg->mul[0]);
+        for (int u = 0; u < cfg->mul[0]; ++u) {
+            double acc = 0.0;
+            for (int k = 0; k < hid; ++k) acc += weights[r0->off + (size_t)u * hid + k] * weights[r1->off + k];
+            c[u] = (float)(cfg->scale * acc / std::sqrt((double)cfg->mul[0]) / std::sqrt((double)hid));
+        }
+        s = dev_upload(M, c, &M->readout);
+        if (s) return fail(s);
+        s = dev_upload(M, M->shift, &M->shift_dev);
+        if (s) return fail(s);
+    }
+    const int H = cfg->mlp_hidden, NB = cfg->n_basis;
+    M->layers.resize(M->T);
+    for (int t = 0; t < M->T; ++t) {
+        LayerDev& L = M->layers[t];
+        std::vector<PathH> paths;
+        block_irreps(cfg, t, L.in_mul, L.y_mul, L.out_mul, paths, L.msg_mul, &L.last);
+        offsets(L.in_mul, L.in_off, &L.h_in_dim);
+        offsets(L.y_mul, L.y_off, &L.y_dim);
+        offsets(L.msg_mul, L.msg_off, &L.m_dim);
+        offsets(L.out_mul, L.out_off, &L.h_out_dim);
+        L.x_dim = L.h_in_dim;
+        for (int l = 0; l < 3; ++l)
+            if (L.y_mul[l] && !L.in_mul[l] && !L.msg_mul[l]) {
+                set_error("block %d: gate input irrep %d has no producer", t);
+                return fail(SEVENNET_EINVAL);
+            }
+        M->h_max = std::max({M->h_max, L.h_in_dim, L.h_out_dim});
+        M->x_max = std::max(M->x_max, L.x_dim);
+        M->y_max = std::max(M->y_max, L.y_dim);
+        M->m_max = std::max(M->m_max, L.m_dim);
+        // conv descriptor
+        ConvDesc& D = L.conv;
+        std::memset(&D, 0, sizeof(D));
+        D.n_paths = (int)paths.size();
+        if (D.n_paths > MAX_PATHS) { set_error("too many paths"); return fail(SEVENNET_EINVAL); }
+        int col = 0, goff = 0;
+        int ch[3] = {0, 0, 0};
+        for (int l = 0; l < 3; ++l) { D.pbeg[l] = D.pend[l] = 0; }
+        for (int p = 0; p < D.n_paths; ++p) {
+            const PathH& q = paths[p];
+            PathDesc& P = D.paths[p];
+            P.l1 = q.l1; P.l2 = q.l2; P.l3 = q.l3;
+            P.kind = coupling_kind(q.l1, q.l2, q.l3);
+            P.mul = q.mul;
+            P.col0 = col;
+            P.x_off = L.in_off[q.l1];
+            P.m_off = L.msg_off[q.l3];
+            P.m_mul = L.msg_mul[q.l3];
+            P.m_ch0 = ch[q.l3];
+            P.g_off = goff;
+            col += q.mul;
+            ch[q.l3] += q.mul;
+            goff += (2 * q.l1 + 1) * (2 * q.l3 + 1);
+        }
+        for (int l = 0; l < 3; ++l) {
+            int b = -1, e = -1;
+            for (int p = 0; p < D.n_paths; ++p)
+                if (D.paths[p].l1 == l) { if (b < 0) b = p; e = p + 1; }
+            D.pbeg[l] = b < 0 ? 0 : b;
+            D.pend[l] = e < 0 ? 0 : e;
+            D.mul_in[l] = L.in_mul[l];
+            D.x_off[l] = L.in_off[l];
+            if (L.in_mul[l]) D.l1max = l;
+        }
+        D.W = col;
+        D.Wpad = ((col + 3) & ~3) + 4;
+        D.H = H;
+        D.n_basis = NB;
+        D.lmax = cfg->lmax;
+        D.x_dim = L.x_dim;
+        D.m_dim = L.m_dim;
+        D.nG = goff;
+        D.r_cut = (float)cfg->r_cut;
+        const double p = cfg->poly_p;
+        D.env_a = (float)((p + 1.0) * (p + 2.0) / 2.0);
+        D.env_b = (float)(p * (p + 2.0));
+        D.env_c = (float)(p * (p + 1.0) / 2.0);
+        D.poly_p = cfg->poly_p;
+        if (!assign_slots(D)) { set_error("block %d: too many channel groups", t); return fail(SEVENNET_EINVAL); }
+        // weights
+        const std::string pre = "L" + std::to_string(t) + ".";
+        sevennet_status s;
+        for (int l = 0; l < 3; ++l) {
+            if (L.in_mul[l]) {
+                const WEntry* e = find(pre + "lin1." + std::to_string(l));
+                s = upload_linear(M, weights + e->off, e->rows, e->cols, 1.0 / std::sqrt((double)e->rows),
+                                  &L.lin1[l], &L.lin1T[l], &L.lin1h[l], &L.lin1Th[l]);
+                if (s) return fail(s);
+            }
+            if (L.in_mul[l] && L.y_mul[l]) {
+                const WEntry* e = find(pre + "sc." + std::to_string(l));
+                s = upload_linear(M, weights + e->off, e->rows, e->cols, 1.0 / std::sqrt((double)e->rows),
+                                  &L.sc[l], &L.scT[l], &L.sch[l], &L.scTh[l]);
+                if (s) return fail(s);
+            }
+            if (L.msg_mul[l] && L.y_mul[l]) {
+                const WEntry* e = find(pre + "lin2." + std::to_string(l));
+                s = upload_linear(M, weights + e->off, e->rows, e->cols, 1.0 / std::sqrt((double)e->rows),
+                                  &L.lin2[l], &L.lin2T[l], &L.lin2h[l], &L.lin2Th[l]);
+                if (s) return fail(s);
+            }
+        }
+        {
+            const WEntry* e0 = find(pre + "mlp0");
+            const WEntry* e1 = find(pre + "mlp1");
+            const WEntry* e2 = find(pre + "mlp2");
+            auto w0 = scaled(weights + e0->off, NB, H, 1.0 / std::sqrt((double)NB), false);
+            auto w1 = scaled(weights + e1->off, H, H, 1.0 / std::sqrt((double)H), false);
+            const double s2 = 1.0 / std::sqrt((double)H) / cfg->avg_num_neigh;
+            auto w2 = scaled(weights + e2->off, H, D.W, s2, false);
+            auto w2T = scaled(weights + e2->off, H, D.W, s2, true);
+            if ((s = dev_upload(M, w0, &L.mlp0))) return fail(s);
+            if ((s = dev_upload(M, w1, &L.mlp1))) return fail(s);
+            if ((s = dev_upload(M, w2, &L.mlp2))) return fail(s);
+            if ((s = dev_upload(M, w2T, &L.mlp2T))) return fail(s);
+            if ((s = dev_upload(M, to_bf16(w2T), &L.mlp2h))) return fail(s);   // [W][H]
+            if ((s = dev_upload(M, to_bf16(w2), &L.mlp2Th))) return fail(s);   // [H][W]
+        }
+    }
+    sevennet_status s = conv_configure(H, M->layers);
+    if (s) return fail(s);
+    if (cudaStreamCreateWithFlags(&M->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaStreamCreate failed");
+        return fail(SEVENNET_ECUDA);
+    }
+    M->ws = new Workspace();
+    *out = M;
+    return SEVENNET_OK;
+}
+
+void sevennet_destroy_model(sevennet_model* M) {
+    if (!M) return;
+    cudaSetDevice(M->device);
+    if (M->stream) cudaStreamSynchronize(M->stream);
+    ws_free(M->ws);
+    for (void* p : M->allocations) cudaFree(p);
+    if (M->stream) cudaStreamDestroy(M->stream);
+    delete M;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ neighbour lists
+struct sevennet_nlist {
+    int device;
+    int64_t n_atoms, n_edges;
+    int* dst = nullptr;    // input-order indices
+    int* src = nullptr;
+    int* shift = nullptr;
+};
+
+namespace sn {
+
+sevennet_status check_batch(const BatchHost& b) {
+    SN_CHECK(b.n_structs >= 1, SEVENNET_EINVAL, "n_structs must be >= 1");
+    SN_CHECK(b.atom_off[0] == 0, SEVENNET_EINVAL, "atom_offsets[0] must be 0");
+    for (int s = 0; s < b.n_structs; ++s)
+        SN_CHECK(b.atom_off[s + 1] >= b.atom_off[s], SEVENNET_EINVAL, "atom_offsets must be non-decreasing");
+    SN_CHECK(b.atom_off[b.n_structs] < (1LL << 30), SEVENNET_EINVAL, "too many atoms");
+    for (double c : b.cells) SN_CHECK(std::isfinite(c), SEVENNET_EINVAL, "cell is not finite");
+    return SEVENNET_OK;
+}
+
+__global__ void map_edges_kernel(int64_t E, const int* __restrict__ perm, const int* __restrict__ dst,
+                                 const int* __restrict__ src, int* __restrict__ odst, int* __restrict__ osrc) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    odst[e] = perm[dst[e]];
+    osrc[e] = perm[src[e]];
+}
+
+__global__ void check_species_kernel(int64_t n, const int32_t* __restrict__ sp, int ns, int* flags) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && (sp[i] < 0 || sp[i] >= ns)) atomicOr(flags + 3, 1);
+}
+
+// Evaluate a batch whose positions and species are already on the device.
+sevennet_status eval_batch(sevennet_model* M, Workspace* ws, const BatchHost& b,
+                           const int32_t* species_dev, const double* pos_dev, sevennet_precision prec,
+                           double* energy_dev, double* forces_dev, double* virial_dev, cudaStream_t st) {
+    SN_TRY(check_batch(b));
+    SN_CHECK(prec == SEVENNET_FP32 || prec == SEVENNET_BF16, SEVENNET_EINVAL, "unknown precision");
+    const int64_t N = b.atom_off[b.n_structs];
+    int64_t E = 0;
+    SN_TRY(build_neighbors(M, ws, b, pos_dev, species_dev, st, &E));
+    if (N > 0) {
+        check_species_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, species_dev, M->cfg.n_species,
+                                                                          ws->flags);
+    }
+    SN_TRY(run_model(M, ws, b, E, prec, energy_dev, forces_dev, virial_dev, st));
+    SN_CUDA(cudaMemcpyAsync(ws->flags_host, ws->flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    SN_CUDA(cudaStreamSynchronize(st));
+    SN_CHECK(ws->flags_host[3] == 0, SEVENNET_EINVAL, "species index out of range");
+    SN_CHECK(ws->flags_host[2] == 0, SEVENNET_ECUDA, "internal error: reverse edge not found");
+    return SEVENNET_OK;
+}
+
+}  // namespace sn
+
+extern "C" {
+
+sevennet_status sevennet_build_neighbors(sevennet_model* M, int64_t n_atoms, const double* pos,
+                                         const double* cell, const int32_t pbc[3], sevennet_nlist** out,
+                                         int64_t* n_edges) {
+    SN_CHECK(M && out && n_edges && cell && (pos || n_atoms == 0), SEVENNET_EINVAL, "NULL argument");
+    SN_CHECK(n_atoms >= 0, SEVENNET_EINVAL, "n_atoms < 0");
+    *out = nullptr;
+    SN_CUDA(cudaSetDevice(M->device));
+    BatchHost b;
+    b.n_structs = 1;
+    b.atom_off = {0, n_atoms};
+    b.cells.assign(cell, cell + 9);
+    b.pbc = {pbc ? pbc[0] : 1, pbc ? pbc[1] : 1, pbc ? pbc[2] : 1};
+    SN_TRY(check_batch(b));
+    for (int64_t i = 0; i < 3 * n_atoms; ++i) SN_CHECK(std::isfinite(pos[i]), SEVENNET_EINVAL, "position not finite");
+    cudaStream_t st = M->stream;
+    double* pos_dev = nullptr;
+    int32_t* sp_dev = nullptr;
+    SN_CUDA(cudaMallocAsync(&pos_dev, std::max<int64_t>(n_atoms, 1) * 3 * sizeof(double), st));
+    SN_CUDA(cudaMallocAsync(&sp_dev, std::max<int64_t>(n_atoms, 1) * sizeof(int32_t), st));
+    if (n_atoms) SN_CUDA(cudaMemcpyAsync(pos_dev, pos, n_atoms * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+    SN_CUDA(cudaMemsetAsync(sp_dev, 0, std::max<int64_t>(n_atoms, 1) * sizeof(int32_t), st));
+    int64_t E = 0;
+    sevennet_status s = build_neighbors(M, M->ws, b, pos_dev, sp_dev, st, &E);
+    if (s == SEVENNET_OK) {
+        auto* nl = new sevennet_nlist();
+        nl->device = M->device;
+        nl->n_atoms = n_atoms;
+        nl->n_edges = E;
+        const size_t e1 = std::max<int64_t>(E, 1);
+        if (cudaMalloc(&nl->dst, e1 * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&nl->src, e1 * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&nl->shift, e1 * 3 * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            sevennet_nlist_destroy(nl);
+            set_error("cudaMalloc failed for the neighbour list");
+            s = SEVENNET_ENOMEM;
+        } else {
+            if (E > 0) {
+                map_edges_kernel<<<(unsigned)((E + 255) / 256), 256, 0, st>>>(E, M->ws->perm, M->ws->dst,
+                                                                              M->ws->src, nl->dst, nl->src);
+                cudaMemcpyAsync(nl->shift, M->ws->shift, E * 3 * sizeof(int), cudaMemcpyDeviceToDevice, st);
+            }
+            if (cudaStreamSynchronize(st) != cudaSuccess) {
+                set_error("neighbour list copy failed: %s", cudaGetErrorString(cudaGetLastError()));
+                sevennet_nlist_destroy(nl);
+                s = SEVENNET_ECUDA;
+            } else {
+                *out = nl;
+                *n_edges = E;
+            }
+        }
+    }
+    cudaFreeAsync(pos_dev, st);
+    cudaFreeAsync(sp_dev, st);
+    return s;
+}
+
+sevennet_status sevennet_nlist_export(const sevennet_nlist* nl, int32_t* dst, int32_t* src, int32_t* shift) {
+    SN_CHECK(nl, SEVENNET_EINVAL, "NULL list");
+    SN_CUDA(cudaSetDevice(nl->device));
+    if (nl->n_edges == 0) return SEVENNET_OK;
+    if (dst) SN_CUDA(cudaMemcpy(dst, nl->dst, nl->n_edges * sizeof(int), cudaMemcpyDeviceToHost));
+    if (src) SN_CUDA(cudaMemcpy(src, nl->src, nl->n_edges * sizeof(int), cudaMemcpyDeviceToHost));
+    if (shift) SN_CUDA(cudaMemcpy(shift, nl->shift, nl->n_edges * 3 * sizeof(int), cudaMemcpyDeviceToHost));
+    return SEVENNET_OK;
+}
+
+void sevennet_nlist_destroy(sevennet_nlist* nl) {
+    if (!nl) return;
+    cudaSetDevice(nl->device);
+    cudaFree(nl->dst);
+    cudaFree(nl->src);
+    cudaFree(nl->shift);
+    delete nl;
+}
+
+sevennet_status sevennet_eval_energy_forces_virial(sevennet_model* M, int64_t n_atoms, const int32_t* species,
+                                                   const double* pos, const double* cell, const int32_t pbc[3],
+                                                   sevennet_precision prec, double* energy, double* forces,
+                                                   double* virial) {
+    SN_CHECK(M && cell && (n_atoms == 0 || (pos && species)), SEVENNET_EINVAL, "NULL argument");
+    SN_CHECK(n_atoms >= 0, SEVENNET_EINVAL, "n_atoms < 0");
+    SN_CUDA(cudaSetDevice(M->device));
+    for (int64_t i = 0; i < 3 * n_atoms; ++i) SN_CHECK(std::isfinite(pos[i]), SEVENNET_EINVAL, "position not finite");
+    for (int64_t i = 0; i < n_atoms; ++i)
+        SN_CHECK(species[i] >= 0 && species[i] < M->cfg.n_species, SEVENNET_EINVAL, "species index out of range");
+    BatchHost b;
+    b.n_structs = 1;
+    b.atom_off = {0, n_atoms};
+    b.cells.assign(cell, cell + 9);
+    b.pbc = {pbc ? pbc[0] : 1, pbc ? pbc[1] : 1, pbc ? pbc[2] : 1};
+    cudaStream_t st = M->stream;
+    const size_t n1 = std::max<int64_t>(n_atoms, 1);
+    double *pos_dev = nullptr, *f_dev = nullptr, *e_dev = nullptr, *w_dev = nullptr;
+    int32_t* sp_dev = nullptr;
+    SN_CUDA(cudaMallocAsync(&pos_dev, n1 * 3 * sizeof(double), st));
+    SN_CUDA(cudaMallocAsync(&f_dev, n1 * 3 * sizeof(double), st));
+    SN_CUDA(cudaMallocAsync(&sp_dev, n1 * sizeof(int32_t), st));
+    SN_CUDA(cudaMallocAsync(&e_dev, 16 * sizeof(double), st));
+    w_dev = e_dev + 4;
+    if (n_atoms) {
+        SN_CUDA(cudaMemcpyAsync(pos_dev, pos, n_atoms * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+        SN_CUDA(cudaMemcpyAsync(sp_dev, species, n_atoms * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    }
+    sevennet_status s = eval_batch(M, M->ws, b, sp_dev, pos_dev, prec, e_dev, f_dev, w_dev, st);
+    if (s == SEVENNET_OK) {
+        if (energy) cudaMemcpyAsync(energy, e_dev, sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (virial) cudaMemcpyAsync(virial, w_dev, 9 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (forces && n_atoms) cudaMemcpyAsync(forces, f_dev, n_atoms * 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            set_error("result copy failed: %s", cudaGetErrorString(cudaGetLastError()));
+            s = SEVENNET_ECUDA;
+        }
+    }
+    cudaFreeAsync(pos_dev, st);
+    cudaFreeAsync(f_dev, st);
+    cudaFreeAsync(sp_dev, st);
+    cudaFreeAsync(e_dev, st);
+    cudaStreamSynchronize(st);
+    return s;
+}
+
+sevennet_status sevennet_eval_batch_dev(sevennet_model* M, int32_t n_structs, const int64_t* atom_offsets,
+                                        const double* cells, const int32_t* pbc, const int32_t* species_dev,
+                                        const double* pos_dev, sevennet_precision prec, double* energy_dev,
+                                        double* forces_dev, double* virial_dev, void* stream) {
+    SN_CHECK(M && atom_offsets && cells && n_structs >= 1, SEVENNET_EINVAL, "bad argument");
+    SN_CUDA(cudaSetDevice(M->device));
+    BatchHost b;
+    b.n_structs = n_structs;
+    b.atom_off.assign(atom_offsets, atom_offsets + n_structs + 1);
+    b.cells.assign(cells, cells + (size_t)n_structs * 9);
+    if (pbc) b.pbc.assign(pbc, pbc + (size_t)n_structs * 3);
+    SN_CHECK(b.atom_off[n_structs] == 0 || (species_dev && pos_dev), SEVENNET_EINVAL, "NULL device array");
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : M->stream;
+    return eval_batch(M, M->ws, b, species_dev, pos_dev, prec, energy_dev, forces_dev, virial_dev, st);
+}
+
+sevennet_status sevennet_conv_dims(const sevennet_model* M, int32_t layer, int32_t* x_dim, int32_t* m_dim) {
+    SN_CHECK(M && layer >= 0 && layer < M->T, SEVENNET_EINVAL, "bad layer");
+    if (x_dim) *x_dim = M->layers[layer].x_dim;
+    if (m_dim) *m_dim = M->layers[layer].m_dim;
+    return SEVENNET_OK;
+}
+
+sevennet_status sevennet_conv_forward_dev(sevennet_model* M, int32_t layer, int64_t n_atoms, int64_t n_edges,
+                                          const int32_t* row_ptr, const int32_t* src, const float* d,
+                                          const float* x, float* m_out, sevennet_precision prec, void* stream) {
+    SN_CHECK(M && layer >= 0 && layer < M->T && n_atoms >= 0 && n_edges >= 0, SEVENNET_EINVAL, "bad argument");
+    SN_CHECK(row_ptr && x && m_out && (n_edges == 0 || (src && d)), SEVENNET_EINVAL, "NULL argument");
+    SN_CUDA(cudaSetDevice(M->device));
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : M->stream;
+    // build (dst, float4 geometry) from the caller's CSR + FP32 displacements
+    int* dst = nullptr;
+    float4* geom = nullptr;
+    const size_t e1 = std::max<int64_t>(n_edges, 1);
+    SN_CUDA(cudaMallocAsync(&dst, e1 * sizeof(int), st));
+    SN_CUDA(cudaMallocAsync(&geom, e1 * sizeof(float4), st));
+    conv_prepare_edges(n_atoms, n_edges, row_ptr, d, dst, geom, st);
+    launch_conv_fwd(M->layers[layer], M->H, prec, n_atoms, n_edges, row_ptr, dst, src, geom, x, m_out, st);
+    SN_CUDA(cudaGetLastError());
+    cudaFreeAsync(dst, st);
+    cudaFreeAsync(geom, st);
+    return SEVENNET_OK;
+}
+
+sevennet_status sevennet_conv_backward_dev(sevennet_model* M, int32_t layer, int64_t n_atoms, int64_t n_edges,
+                                           const int32_t* row_ptr, const int32_t* src, const float* d,
+                                           const float* x, const float* g_m, float* g_x, float* g_d,
+                                           sevennet_precision prec, void* stream) {
+    SN_CHECK(M && layer >= 0 && layer < M->T && n_atoms >= 0 && n_edges >= 0, SEVENNET_EINVAL, "bad argument");
+    SN_CHECK(row_ptr && x && g_m && g_x && (n_edges == 0 || (src && d && g_d)), SEVENNET_EINVAL, "NULL argument");
+    SN_CUDA(cudaSetDevice(M->device));
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : M->stream;
+    int* dst = nullptr;
+    float4* geom = nullptr;
+    const size_t e1 = std::max<int64_t>(n_edges, 1);
+    SN_CUDA(cudaMallocAsync(&dst, e1 * sizeof(int), st));
+    SN_CUDA(cudaMallocAsync(&geom, e1 * sizeof(float4), st));
+    conv_prepare_edges(n_atoms, n_edges, row_ptr, d, dst, geom, st);
+    SN_CUDA(cudaMemsetAsync(g_x, 0, (size_t)std::max<int64_t>(n_atoms, 1) * M->layers[layer].x_dim * sizeof(float), st));
+    launch_conv_bwd(M->layers[layer], M->H, prec, n_atoms, n_edges, row_ptr, dst, src, geom, x, g_m, g_x, g_d, st);
+    SN_CUDA(cudaGetLastError());
+    cudaFreeAsync(dst, st);
+    cudaFreeAsync(geom, st);
+    return SEVENNET_OK;
+}
+
+}  // extern "C"

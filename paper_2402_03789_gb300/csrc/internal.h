@@ -1,0 +1,264 @@
+// Internal declarations of the SevenNet GB300 library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "sevennet.h"
+
+namespace sn {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+extern thread_local std::string g_last_error;
+
+#define SN_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            ::sn::set_error("%s:%d: %s: %s", __FILE__, __LINE__, #call,            \
+                            cudaGetErrorString(e_));                               \
+            return SEVENNET_ECUDA;                                                 \
+        }                                                                          \
+    } while (0)
+
+#define SN_CHECK(cond, code, ...)                                                  \
+    do {                                                                           \
+        if (!(cond)) {                                                             \
+            ::sn::set_error(__VA_ARGS__);                                          \
+            return (code);                                                         \
+        }                                                                          \
+    } while (0)
+
+#define SN_TRY(expr)                                                               \
+    do {                                                                           \
+        sevennet_status s_ = (expr);                                               \
+        if (s_ != SEVENNET_OK) return s_;                                          \
+    } while (0)
+
+// ---------------------------------------------------------------- model
+constexpr int MAX_PATHS = 16;
+constexpr int CONV_THREADS = 256;
+constexpr int CONV_WARPS = CONV_THREADS / 32;
+constexpr int MAX_SLOTS = 12;
+constexpr int EC = 32;                 // edges per chunk in the convolution kernels
+constexpr int MAX_NB = 16;             // radial basis functions
+constexpr int MAX_LMAX = 2;
+
+// kind = canonical index of the coupling (l1, l2, l3) among the 15 with l <= 2
+__host__ __device__ constexpr int coupling_kind(int l1, int l2, int l3) {
+    // table order: l1-major, then l2, then l3 (matches the path order of a block)
+    int k = 0;
+    for (int a = 0; a <= 2; ++a)
+        for (int b = 0; b <= 2; ++b)
+            for (int c = (a > b ? a - b : b - a); c <= (a + b < 2 ? a + b : 2); ++c) {
+                if (a == l1 && b == l2 && c == l3) return k;
+                ++k;
+            }
+    return -1;
+}
+
+struct PathDesc {
+    int32_t l1, l2, l3, kind;
+    int32_t mul;      // channels of the path (= multiplicity of l1 in the block input)
+    int32_t col0;     // first radial-MLP output column of the path
+    int32_t x_off;    // offset of the l1 block inside an x row
+    int32_t m_off;    // offset of the l3 block inside a message row
+    int32_t m_mul;    // channels of the l3 message block
+    int32_t m_ch0;    // first channel of this path inside the l3 block
+    int32_t g_off;    // offset of this path's G matrix in the per-edge buffer
+};
+
+// Everything a convolution kernel needs to know about one block.
+struct ConvDesc {
+    int32_t n_paths;
+    int32_t W;          // radial MLP output width (sum of path channels)
+    int32_t Wpad;       // row stride of the per-edge weight tile in shared memory
+    int32_t H;          // hidden width of the radial MLP
+    int32_t n_basis;
+    int32_t lmax;       // spherical-harmonic degree
+    int32_t x_dim;      // row width of x (block input after linear_1)
+    int32_t m_dim;      // row width of the messages
+    int32_t nG;         // floats of G per edge
+    int32_t l1max;
+    int32_t mul_in[3];  // multiplicity of l in the block input (0 = absent)
+    int32_t x_off[3];
+    int32_t pbeg[3], pend[3];   // paths with l1 = l occupy [pbeg, pend)
+    float r_cut;
+    float env_a, env_b, env_c;  // envelope coefficients
+    int32_t poly_p;
+    PathDesc paths[MAX_PATHS];
+    int16_t n_slots[CONV_WARPS];
+    int16_t slot_group[CONV_WARPS][MAX_SLOTS];  // (path << 8) | channel block
+};
+
+// One row-block matrix product of a per-irrep linear: rows are (atom, m)
+// pairs, row r -> atom v = r / R, component m = r % R, A row at
+// A + v*lda + a_off + m*K, C row at C + v*ldc + c_off + m*N.
+struct GemmProb {
+    const float* A;
+    const float* B;            // [K][N] row-major FP32 (pre-scaled)
+    const __nv_bfloat16* Bh;   // [N][K] BF16 transpose, for the tensor-core path
+    float* C;
+    int64_t n_atoms;
+    int32_t R, K, N;
+    int32_t lda, a_off, ldc, c_off;
+    int32_t accumulate;        // 1: C += A B, 0: C = A B
+};
+constexpr int MAX_GEMM_PROBS = 8;
+struct GemmBatch {
+    int32_t n;
+    GemmProb p[MAX_GEMM_PROBS];
+};
+
+struct LayerDev {
+    ConvDesc conv;
+    int x_dim, y_dim, h_in_dim, h_out_dim, m_dim;
+    int in_mul[3], y_mul[3], msg_mul[3], out_mul[3];
+    int in_off[3], y_off[3], msg_off[3], out_off[3];
+    bool last;
+    // device weights, pre-scaled by 1/sqrt(fan_in) (and 1/avg_num_neigh for mlp2)
+    float* mlp0 = nullptr;   // [NB][H]
+    float* mlp1 = nullptr;   // [H][H]
+    float* mlp2 = nullptr;   // [H][W]
+    float* mlp0T = nullptr;  // [H][NB]
+    float* mlp1T = nullptr;  // [H][H]
+    float* mlp2T = nullptr;  // [W][H]
+    __nv_bfloat16* mlp2h = nullptr;   // [W][H]  (N-major for mma B operand)
+    __nv_bfloat16* mlp2Th = nullptr;  // [H][W]
+    float* lin1[3] = {};  float* lin1T[3] = {};  __nv_bfloat16* lin1h[3] = {};  __nv_bfloat16* lin1Th[3] = {};
+    float* sc[3] = {};    float* scT[3] = {};    __nv_bfloat16* sch[3] = {};    __nv_bfloat16* scTh[3] = {};
+    float* lin2[3] = {};  float* lin2T[3] = {};  __nv_bfloat16* lin2h[3] = {};  __nv_bfloat16* lin2Th[3] = {};
+};
+
+struct Workspace;
+
+}  // namespace sn
+
+struct sevennet_model {
+    int device = 0;
+    sevennet_model_config cfg{};
+    std::vector<double> shift;
+    int T = 0, lmax = 0, H = 0, NB = 0;
+    int h_max = 0, x_max = 0, y_max = 0, m_max = 0;
+    std::vector<sn::LayerDev> layers;
+    float* embed = nullptr;     // [n_species][mul0]
+    float* readout = nullptr;   // [mul0] = scale * R0 R1 / sqrt(mul0 hid)
+    double* shift_dev = nullptr;
+    cudaStream_t stream = nullptr;
+    sn::Workspace* ws = nullptr;
+    std::vector<void*> allocations;
+};
+
+namespace sn {
+
+// ---------------------------------------------------------------- workspace
+struct Workspace {
+    int64_t cap_atoms = 0, cap_edges = 0, cap_bins = 0, cap_structs = 0;
+    // neighbour build (internal atom order = cell-sorted)
+    int* bin_of = nullptr;        // [N] bin of each input atom
+    int* bin_count = nullptr;     // [bins+1]
+    int* bin_start = nullptr;     // [bins+1]
+    int* bin_fill = nullptr;      // [bins]
+    int* perm = nullptr;          // [N] internal -> input index
+    int* struct_of = nullptr;     // [N] internal atom -> structure
+    double* pos_s = nullptr;      // [N][3] positions in internal order (as given)
+    double* frac_floor = nullptr; // [N][3] integer image of each internal atom
+    int* species_s = nullptr;     // [N]
+    int* row_ptr = nullptr;       // [N+1]
+    int* row_cnt = nullptr;       // [N+1]
+    int* dst = nullptr;           // [E]
+    int* src = nullptr;           // [E]
+    int* shift = nullptr;         // [E][3]
+    int* rev = nullptr;           // [E]
+    float4* geom = nullptr;       // [E] (d, r)
+    // per-structure descriptors (device)
+    double* cells = nullptr;      // [S][9]
+    double* inv_cells = nullptr;  // [S][9]
+    int* sdesc = nullptr;         // [S][16] bins, offsets, search ranges, pbc
+    int64_t* atom_off = nullptr;  // [S+1]
+    // model activations
+    float* h = nullptr;           // [N][h_max]
+    float* xs = nullptr;          // [T][N][x_max]
+    float* ys = nullptr;          // [T][N][y_max]
+    float* m = nullptr;           // [N][m_max] (messages, then their gradients)
+    float* gy = nullptr;          // [N][y_max]
+    float* gx = nullptr;          // [N][x_max]
+    float* gh = nullptr;          // [N][h_max]
+    float* gd = nullptr;          // [E][3]
+    double* e_atom = nullptr;     // [N]
+    double* w_atom = nullptr;     // [N][9]
+    double* f_s = nullptr;        // [N][3] forces, internal order
+    int* flags = nullptr;         // [8] device status words
+    int* flags_host = nullptr;    // pinned mirror
+    std::vector<void*> allocs;
+};
+
+// host helpers implemented in the .cu files
+sevennet_status ws_reserve(sevennet_model* M, Workspace* ws, int64_t n_atoms, int64_t n_edges,
+                           int64_t n_bins, int64_t n_structs, cudaStream_t st);
+void ws_free(Workspace* ws);
+
+struct BatchHost {
+    int32_t n_structs;
+    std::vector<int64_t> atom_off;   // [S+1]
+    std::vector<double> cells;       // [S][9]
+    std::vector<int32_t> pbc;        // [S][3]
+};
+
+// Neighbour build for a batch; positions/species are device arrays in input
+// order.  Leaves ws->row_ptr/src/dst/shift/geom/rev and the internal order.
+sevennet_status build_neighbors(sevennet_model* M, Workspace* ws, const BatchHost& b,
+                                const double* pos_dev, const int32_t* species_dev,
+                                cudaStream_t st, int64_t* n_edges_out);
+
+// Model evaluation on the internal order prepared by build_neighbors.
+sevennet_status run_model(sevennet_model* M, Workspace* ws, const BatchHost& b, int64_t n_edges,
+                          sevennet_precision prec, double* energy_dev, double* forces_dev,
+                          double* virial_dev, cudaStream_t st);
+
+// kernels launchers (conv.cu / node.cu)
+void launch_conv_fwd(const LayerDev& L, int H, sevennet_precision prec, int64_t n_atoms,
+                     int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
+                     const float4* geom, const float* x, float* m, cudaStream_t st);
+void launch_conv_bwd(const LayerDev& L, int H, sevennet_precision prec, int64_t n_atoms,
+                     int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
+                     const float4* geom, const float* x, const float* gm, float* gx,
+                     float* gd, cudaStream_t st);
+sevennet_status conv_configure(int H, const std::vector<LayerDev>& layers);
+void launch_gemm(const GemmBatch& b, sevennet_precision prec, cudaStream_t st);
+void launch_embed(const float* table, const int* species, int64_t n, int mul0, int n_species, float* h,
+                  cudaStream_t st);
+void launch_gate_fwd(const LayerDev& L, int mul0, const int* mul, int lmax, int64_t n,
+                     const float* y, float* h, cudaStream_t st);
+void launch_gate_bwd(const LayerDev& L, int mul0, const int* mul, int lmax, int64_t n,
+                     const float* y, const float* gh, const float* readout, float* gy,
+                     cudaStream_t st);
+void launch_readout(const float* h, int h_dim, const float* c, const double* shift,
+                    const int* species, int64_t n, int mul0, int n_species, double* e_atom, cudaStream_t st);
+void launch_forces(int64_t n, const int* row_ptr, const int* rev, const float* gd,
+                   const float4* geom, double* f_s, double* w_atom, cudaStream_t st);
+void launch_reduce_structs(int32_t n_structs, const int64_t* atom_off, const double* e_atom,
+                           const double* w_atom, double* energy, double* virial, cudaStream_t st);
+void launch_scatter_forces(int64_t n, const int* perm, const double* f_s, double* forces,
+                           cudaStream_t st);
+
+int num_sms(int device);
+
+// dst and (d, |d|) of caller-provided CSR edges (conv entry points)
+void conv_prepare_edges(int64_t n_atoms, int64_t n_edges, const int* row_ptr, const float* d,
+                        int* dst, float4* geom, cudaStream_t st);
+
+// shared by the C ABI front ends (api.cu, md_server.cu)
+sevennet_status eval_batch(sevennet_model* M, Workspace* ws, const BatchHost& b,
+                           const int32_t* species_dev, const double* pos_dev,
+                           sevennet_precision prec, double* energy_dev, double* forces_dev,
+                           double* virial_dev, cudaStream_t st);
+sevennet_status check_batch(const BatchHost& b);
+
+}  // namespace sn

@@ -1,0 +1,333 @@
+// Node-level kernels of the interaction blocks and the readout.
+//
+//  * per-irrep linears (linear_1, self-connection, linear_2; Figure 2b and the
+//    self-connection-as-linear of Sec. 5.1): out[v, m, :] = in[v, m, :] @ W,
+//    W pre-scaled by 1/sqrt(fan_in); rows are (atom, m) pairs.
+//  * gate (NequIP's equivariant nonlinearity, Sec. 3.2) and its adjoint.
+//  * embedding h1 = W_emb[Z] and the atomwise readout (Eq. 1).
+//  * forces F_v = sum_w (F_vw - F_wv) (Eq. 6) from the per-edge gradients
+//    F_vw = dE/dd_vw accumulated over blocks (Eq. 5), and the atom virials
+//    -sum_e F_e (x) d_e, both summed in FP64.
+#include "internal.h"
+
+namespace sn {
+
+__device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + expf(-x)); }
+__device__ __forceinline__ float silu_(float x) { return x * sigm(x); }
+__device__ __forceinline__ float dsilu_(float x) {
+    float s = sigm(x);
+    return s * (1.0f + x * (1.0f - s));
+}
+
+// ---------------------------------------------------------------- FP32 GEMM
+// 64 x 64 output tile, 256 threads, 4 x 4 per thread, K slices of 16.
+__global__ void __launch_bounds__(256)
+gemm_f32_kernel(const GemmBatch batch) {
+    const GemmProb& P = batch.p[blockIdx.z];
+    const int64_t rows = P.n_atoms * P.R;
+    const int64_t r0 = (int64_t)blockIdx.x * 64;
+    const int n0 = blockIdx.y * 64;
+    if (r0 >= rows || n0 >= P.N) return;
+    __shared__ __align__(16) float sA[16][68];
+    __shared__ __align__(16) float sB[16][64];
+    const int t = threadIdx.x;
+    const int tr = t / 16, tc = t % 16;
+    float acc[4][4] = {};
+    // A loader: row = t / 4 (0..63), k quad = t % 4
+    const int lrow = t / 4, lkq = t % 4;
+    const int64_t arow = r0 + lrow;
+    const float* aptr = nullptr;
+    if (arow < rows) {
+        const int64_t v = arow / P.R;
+        const int mm = (int)(arow % P.R);
+        aptr = P.A + v * P.lda + P.a_off + (int64_t)mm * P.K;
+    }
+    const int bk = t / 16, bc = t % 16;
+    for (int k0 = 0; k0 < P.K; k0 += 16) {
+        float4 av = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (aptr) av = *reinterpret_cast<const float4*>(aptr + k0 + 4 * lkq);
+        sA[4 * lkq + 0][lrow] = av.x;
+        sA[4 * lkq + 1][lrow] = av.y;
+        sA[4 * lkq + 2][lrow] = av.z;
+        sA[4 * lkq + 3][lrow] = av.w;
+        float4 bv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n0 + 4 * bc < P.N)
+            bv = __ldg(reinterpret_cast<const float4*>(P.B + (int64_t)(k0 + bk) * P.N + n0 + 4 * bc));
+        *reinterpret_cast<float4*>(&sB[bk][4 * bc]) = bv;
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            const float4 a = *reinterpret_cast<const float4*>(&sA[kk][4 * tr]);
+            const float4 b = *reinterpret_cast<const float4*>(&sB[kk][4 * tc]);
+            const float aa[4] = {a.x, a.y, a.z, a.w};
+            const float bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(aa[i], bb[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    const int col = n0 + 4 * tc;
+    if (col >= P.N) return;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t row = r0 + 4 * tr + i;
+        if (row >= rows) break;
+        const int64_t v = row / P.R;
+        const int mm = (int)(row % P.R);
+        float* cp = P.C + v * P.ldc + P.c_off + (int64_t)mm * P.N + col;
+        float4 o = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        if (P.accumulate) {
+            const float4 c = *reinterpret_cast<const float4*>(cp);
+            o.x += c.x; o.y += c.y; o.z += c.z; o.w += c.w;
+        }
+        *reinterpret_cast<float4*>(cp) = o;
+    }
+}
+
+void launch_gemm(const GemmBatch& b, sevennet_precision prec, cudaStream_t st) {
+    (void)prec;
+    if (b.n == 0) return;
+    int64_t max_rows = 0;
+    int max_n = 0;
+    for (int i = 0; i < b.n; ++i) {
+        max_rows = std::max<int64_t>(max_rows, b.p[i].n_atoms * b.p[i].R);
+        max_n = std::max(max_n, b.p[i].N);
+    }
+    if (max_rows == 0) return;
+    dim3 grid((unsigned)((max_rows + 63) / 64), (unsigned)((max_n + 63) / 64), (unsigned)b.n);
+    gemm_f32_kernel<<<grid, 256, 0, st>>>(b);
+}
+
+// ---------------------------------------------------------------- embedding
+__device__ __forceinline__ int clamp_species(int s, int ns) { return s < 0 ? 0 : (s >= ns ? ns - 1 : s); }
+
+// Out-of-range species are clamped here (no out-of-bounds read) and reported
+// as an error by the host after the evaluation.
+__global__ void embed_kernel(const float* __restrict__ table, const int* __restrict__ species,
+                             int64_t n, int mul0, int n_species, float* __restrict__ h) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * mul0) return;
+    const int64_t v = i / mul0;
+    const int u = (int)(i % mul0);
+    h[i] = table[(int64_t)clamp_species(species[v], n_species) * mul0 + u];
+}
+
+void launch_embed(const float* table, const int* species, int64_t n, int mul0, int n_species, float* h,
+                  cudaStream_t st) {
+    const int64_t tot = n * mul0;
+    if (tot == 0) return;
+    embed_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(table, species, n, mul0, n_species, h);
+}
+
+// ---------------------------------------------------------------- gate
+struct GateDims {
+    int mul0, ng, lmax, y_dim, h_dim;
+    int mul[3], y_off[3], h_off[3], goff[3];
+    int last;
+};
+
+static GateDims gate_dims(const LayerDev& L, int mul0, const int* mul, int lmax) {
+    GateDims g{};
+    g.mul0 = mul0;
+    g.lmax = lmax;
+    g.y_dim = L.y_dim;
+    g.h_dim = L.h_out_dim;
+    g.last = L.last ? 1 : 0;
+    int go = 0;
+    for (int l = 0; l <= 2; ++l) {
+        g.mul[l] = (l <= lmax) ? mul[l] : 0;
+        g.y_off[l] = L.y_off[l];
+        g.h_off[l] = L.out_off[l];
+        if (l >= 1 && l <= lmax) { g.goff[l] = go; go += mul[l]; }
+    }
+    g.ng = go;
+    return g;
+}
+
+__global__ void gate_fwd_kernel(const GateDims G, int64_t n, const float* __restrict__ y,
+                                float* __restrict__ h) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * G.h_dim) return;
+    const int64_t v = i / G.h_dim;
+    const int j = (int)(i % G.h_dim);
+    const float* yr = y + v * G.y_dim;
+    if (G.last || j < G.mul0) {
+        h[i] = silu_(yr[j]);
+        return;
+    }
+    int l = 1;
+    if (G.lmax >= 2 && j >= G.h_off[2]) l = 2;
+    const int r = j - G.h_off[l];
+    const int u = r % G.mul[l];
+    const float gate = silu_(yr[G.mul0 + G.goff[l] + u]);
+    h[i] = yr[G.y_off[l] + r] * gate;
+}
+
+void launch_gate_fwd(const LayerDev& L, int mul0, const int* mul, int lmax, int64_t n,
+                     const float* y, float* h, cudaStream_t st) {
+    const GateDims G = gate_dims(L, mul0, mul, lmax);
+    const int64_t tot = n * G.h_dim;
+    if (tot == 0) return;
+    gate_fwd_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(G, n, y, h);
+}
+
+// gy = dE/dy from gh = dE/dh (or, for the last block, the readout vector)
+__global__ void gate_bwd_kernel(const GateDims G, int64_t n, const float* __restrict__ y,
+                                const float* __restrict__ gh, const float* __restrict__ readout,
+                                float* __restrict__ gy) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * G.y_dim) return;
+    const int64_t v = i / G.y_dim;
+    const int j = (int)(i % G.y_dim);
+    const float* yr = y + v * G.y_dim;
+    if (G.last) {
+        gy[i] = readout[j] * dsilu_(yr[j]);
+        return;
+    }
+    const float* ghr = gh + v * G.h_dim;
+    if (j < G.mul0) {
+        gy[i] = ghr[j] * dsilu_(yr[j]);
+        return;
+    }
+    if (j < G.mul0 + G.ng) {               // a gate scalar
+        const int gidx = j - G.mul0;
+        const int l = (G.lmax >= 2 && gidx >= G.goff[2]) ? 2 : 1;
+        const int u = gidx - G.goff[l];
+        float s = 0.0f;
+        for (int mm = 0; mm < 2 * l + 1; ++mm) {
+            const int off = mm * G.mul[l] + u;
+            s = fmaf(ghr[G.h_off[l] + off], yr[G.y_off[l] + off], s);
+        }
+        gy[i] = s * dsilu_(yr[j]);
+        return;
+    }
+    int l = 1;
+    if (G.lmax >= 2 && j >= G.y_off[2]) l = 2;
+    const int r = j - G.y_off[l];
+    const int u = r % G.mul[l];
+    gy[i] = ghr[G.h_off[l] + r] * silu_(yr[G.mul0 + G.goff[l] + u]);
+}
+
+void launch_gate_bwd(const LayerDev& L, int mul0, const int* mul, int lmax, int64_t n,
+                     const float* y, const float* gh, const float* readout, float* gy,
+                     cudaStream_t st) {
+    const GateDims G = gate_dims(L, mul0, mul, lmax);
+    const int64_t tot = n * G.y_dim;
+    if (tot == 0) return;
+    gate_bwd_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(G, n, y, gh, readout, gy);
+}
+
+// ---------------------------------------------------------------- readout
+__global__ void readout_kernel(const float* __restrict__ h, int h_dim, const float* __restrict__ c,
+                               const double* __restrict__ shift, const int* __restrict__ species,
+                               int64_t n, int mul0, int n_species, double* __restrict__ e_atom) {
+    const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (v >= n) return;
+    float s = 0.0f;
+    for (int u = lane; u < mul0; u += 32) s = fmaf(h[v * h_dim + u], c[u], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) e_atom[v] = (double)s + shift[clamp_species(species[v], n_species)];
+}
+
+void launch_readout(const float* h, int h_dim, const float* c, const double* shift,
+                    const int* species, int64_t n, int mul0, int n_species, double* e_atom, cudaStream_t st) {
+    if (n == 0) return;
+    const int64_t threads = n * 32;
+    readout_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(h, h_dim, c, shift, species,
+                                                                      n, mul0, n_species, e_atom);
+}
+
+// ---------------------------------------------------------------- forces / virial
+__global__ void forces_kernel(int64_t n, const int* __restrict__ row_ptr, const int* __restrict__ rev,
+                              const float* __restrict__ gd, const float4* __restrict__ geom,
+                              double* __restrict__ f, double* __restrict__ w) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    double fx = 0, fy = 0, fz = 0;
+    double wv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+        const float* g = gd + (int64_t)e * 3;
+        const float* gr = gd + (int64_t)rev[e] * 3;
+        const double g0 = g[0], g1 = g[1], g2 = g[2];
+        fx += g0 - (double)gr[0];
+        fy += g1 - (double)gr[1];
+        fz += g2 - (double)gr[2];
+        const float4 d = geom[e];
+        const double dd[3] = {d.x, d.y, d.z};
+        const double gg[3] = {g0, g1, g2};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) wv[a * 3 + b] -= gg[a] * dd[b];
+    }
+    f[v * 3 + 0] = fx;
+    f[v * 3 + 1] = fy;
+    f[v * 3 + 2] = fz;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) w[v * 9 + k] = wv[k];
+}
+
+void launch_forces(int64_t n, const int* row_ptr, const int* rev, const float* gd,
+                   const float4* geom, double* f_s, double* w_atom, cudaStream_t st) {
+    if (n == 0) return;
+    forces_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, row_ptr, rev, gd, geom, f_s, w_atom);
+}
+
+// One CTA per structure: fixed-order FP64 sums of atom energies and virials.
+__global__ void reduce_structs_kernel(const int64_t* __restrict__ atom_off,
+                                      const double* __restrict__ e_atom,
+                                      const double* __restrict__ w_atom, double* __restrict__ energy,
+                                      double* __restrict__ virial) {
+    const int s = blockIdx.x;
+    const int64_t a0 = atom_off[s], a1 = atom_off[s + 1];
+    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t v = a0 + threadIdx.x; v < a1; v += blockDim.x) {
+        acc[0] += e_atom[v];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[1 + k] += w_atom[v * 9 + k];
+    }
+    __shared__ double red[10][256];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) red[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) {
+#pragma unroll
+            for (int k = 0; k < 10; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (energy) energy[s] = red[0][0];
+        if (virial)
+            for (int k = 0; k < 9; ++k) virial[s * 9 + k] = red[1 + k][0];
+    }
+}
+
+void launch_reduce_structs(int32_t n_structs, const int64_t* atom_off, const double* e_atom,
+                           const double* w_atom, double* energy, double* virial, cudaStream_t st) {
+    if (n_structs == 0) return;
+    reduce_structs_kernel<<<n_structs, 256, 0, st>>>(atom_off, e_atom, w_atom, energy, virial);
+}
+
+__global__ void scatter_forces_kernel(int64_t n, const int* __restrict__ perm,
+                                      const double* __restrict__ f_s, double* __restrict__ forces) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t o = perm[i];
+    forces[o * 3 + 0] = f_s[i * 3 + 0];
+    forces[o * 3 + 1] = f_s[i * 3 + 1];
+    forces[o * 3 + 2] = f_s[i * 3 + 2];
+}
+
+void launch_scatter_forces(int64_t n, const int* perm, const double* f_s, double* forces,
+                           cudaStream_t st) {
+    if (n == 0 || !forces) return;
+    scatter_forces_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, perm, f_s, forces);
+}
+
+}  // namespace sn

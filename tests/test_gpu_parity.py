@@ -1,0 +1,92 @@
+"""GPU parity of the full E / F / virial path against the FP64 oracle.
+
+Tolerances: FP32 path |dE|/N <= 1e-6 eV, force relative RMS <= 1e-5, virial
+relative Frobenius <= 1e-5; BF16 path force relative RMS <= 5e-3.  The edge set
+must equal the oracle's after sorting (pairs within 1e-6 A of r_c excluded).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import (MODEL_SEVENNET0, MODEL_TINY, make_workload, normal_weights,
+                   random_structure)
+from gpu_common import get_model, edge_set, errors
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    out = []
+    s, spec = make_workload("sio2_192")
+    out.append(("sio2_192_tiny", s, spec))
+    s, spec = make_workload("sio2_192_l2")
+    out.append(("sio2_192_5layer", s, spec))
+    out.append(("ragged_250_5layer", random_structure({"Si": 83, "O": 167}, 2.2, 1.6, seed=11), MODEL_SEVENNET0))
+    out.append(("si3n4_16_selfimages", random_structure({"Si": 6, "N": 8, "O": 2}, 3.1, 1.5, seed=12), MODEL_SEVENNET0))
+    return out
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name,s,spec", CASES, ids=[c[0] for c in CASES])
+def test_neighbor_edge_set_matches_oracle(name, s, spec):
+    model = get_model(spec)
+    dst, src, sh = model.neighbors(s.pos, s.cell)
+    od, os_, osh = oracle.neighbor_list(s.pos, s.cell, spec.r_cut)
+    a = edge_set(dst, src, sh, s.pos, s.cell, spec.r_cut)
+    b = edge_set(od, os_, osh, s.pos, s.cell, spec.r_cut)
+    assert a == b
+    assert len(dst) == len(set(zip(dst, src, map(tuple, sh))))   # no duplicates
+
+
+def test_neighbor_edge_set_triclinic_unwrapped():
+    rng = np.random.default_rng(3)
+    cell = np.array([[7.0, 0.0, 0.0], [2.1, 6.5, 0.0], [-1.3, 1.7, 7.4]])
+    s = random_structure({"Si": 20, "O": 20}, 2.2, 1.6, seed=21)
+    frac = rng.uniform(0, 1, (40, 3))
+    pos = frac @ cell + rng.integers(-3, 4, (40, 3)) @ cell      # far outside the cell
+    model = get_model(MODEL_TINY)
+    dst, src, sh = model.neighbors(pos, cell)
+    od, os_, osh = oracle.neighbor_list_bruteforce(pos, cell, 5.0)
+    assert edge_set(dst, src, sh, pos, cell, 5.0) == edge_set(od, os_, osh, pos, cell, 5.0)
+
+
+@pytest.mark.parametrize("name,s,spec", CASES, ids=[c[0] for c in CASES])
+def test_fp32_energy_forces_virial(name, s, spec):
+    model = get_model(spec)
+    w = normal_weights(oracle.n_params(spec))
+    E, F, W = model.evaluate(s.pos, s.cell, s.species, precision="fp32")
+    Eo, Fo, Wo, *_ = oracle.energy_forces_virial(spec, w, s.species, s.pos, s.cell)
+    e_pa, f_rel, w_rel = errors(E, F, W, Eo, Fo, Wo, s.n_atoms)
+    print(f"{name}: |dE|/N={e_pa:.2e} F={f_rel:.2e} W={w_rel:.2e}")
+    assert e_pa <= 1e-6
+    assert f_rel <= 1e-5
+    assert w_rel <= 1e-5
+
+
+def test_fp32_isolated_atoms_and_empty():
+    spec = MODEL_TINY
+    model = get_model(spec)
+    w = normal_weights(oracle.n_params(spec))
+    cell = np.eye(3) * 30.0
+    pos = np.array([[0.0, 0.0, 0.0], [12.0, 0.0, 0.0], [0.0, 13.0, 0.0]])
+    sp = np.array([0, 1, 2])
+    E, F, W = model.evaluate(pos, cell, sp)
+    Eo, Fo, Wo, *_ = oracle.energy_forces_virial(spec, w, sp, pos, cell)
+    assert abs(E - Eo) <= 1e-6 * 3 and np.abs(F).max() == 0.0 and np.abs(W).max() == 0.0
+    E0, F0, W0 = model.evaluate(np.zeros((0, 3)), cell, np.zeros(0, np.int32))
+    assert E0 == 0.0 and F0.shape == (0, 3)
+
+
+def test_bad_inputs_rejected():
+    import paper_2402_03789_gb300 as sn
+    model = get_model(MODEL_TINY)
+    cell = np.eye(3) * 10.0
+    with pytest.raises(sn.SevenNetError):
+        model.evaluate(np.array([[0.0, 0, 0], [1.0, 1, 1]]), cell, np.array([0, 7]))
+    with pytest.raises(sn.SevenNetError):
+        model.evaluate(np.array([[1.0, 1, 1], [1.0, 1, 1]]), cell, np.array([0, 1]))
+    with pytest.raises(sn.SevenNetError):
+        model.evaluate(np.array([[0.0, 0, 0]]), np.zeros((3, 3)), np.array([0]))
