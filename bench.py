@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Throughput of one SevenNet energy + force + virial evaluation on a GB300.
+
+A step is one full evaluation (cell-list neighbour build, five interaction
+blocks forward, the hand-written adjoint, forces and virial) of the
+24,000-atom SiO2 cell with the 5-layer 128x0e+64x1e+32x2e model, inputs
+resident in HBM.  metric: atom-steps/s (higher is better).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
+  python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
+
+Under torchrun (N > 1) every rank evaluates its own replica (the evaluation
+does not shard: replicas only); value = all ranks' atom-steps / the slowest
+rank's time.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom-steps/s (E+F+virial)"
+UNIT = "atom-steps/s"
+WORKLOAD = "sio2_24000"
+
+# non-zero real Clebsch-Gordan coefficients of each coupling (l1, l2, l3)
+CG_NNZ = {(0, 0, 0): 1, (0, 1, 1): 3, (0, 2, 2): 5, (1, 0, 1): 3, (1, 1, 0): 3, (1, 1, 1): 6,
+          (1, 1, 2): 11, (1, 2, 1): 11, (1, 2, 2): 16, (2, 0, 2): 5, (2, 1, 1): 11, (2, 1, 2): 16,
+          (2, 2, 0): 5, (2, 2, 1): 16, (2, 2, 2): 25}
+
+
+def block_paths(spec, t):
+    lmax = len(spec.mul) - 1
+    first, last = t == 0, t == spec.n_layers - 1
+    in_mul = {0: spec.mul[0]} if first else {l: spec.mul[l] for l in range(lmax + 1)}
+    out = []
+    for l1 in sorted(in_mul):
+        for l2 in range(lmax + 1):
+            for l3 in range(abs(l1 - l2), min(l1 + l2, lmax) + 1):
+                if last and l3 != 0:
+                    continue
+                out.append((l1, l2, l3, in_mul[l1]))
+    return out
+
+
+def conv_flops_per_edge(spec, t, adjoint):
+    """Algorithmic FLOPs of the fused convolution kernel per edge for block t."""
+    H, NB = spec.mlp_hidden, spec.n_basis
+    paths = block_paths(spec, t)
+    W = sum(p[3] for p in paths)
+    mlp = 2 * (NB * H + H * H + H * W)
+    g = sum(2 * CG_NNZ[p[:3]] for p in paths)                 # G matrices
+    if not adjoint:
+        tp = sum(2 * mu * ((2 * l1 + 1) * (2 * l3 + 1) + (2 * l3 + 1)) for l1, l2, l3, mu in paths)
+        return mlp + g + tp
+    tp = sum(2 * mu * ((2 * l1 + 1) * (2 * l3 + 1) + 2 * (2 * l1 + 1) + CG_NNZ[(l1, l2, l3)])
+             for l1, l2, l3, mu in paths)
+    return 2 * mlp + g + tp            # forward recompute + input gradient of the MLP
+
+
+def fp32_alu_peak_tflops(n_sm, clock_mhz):
+    """FFMA peak: SMs x 128 FP32 lanes x 2 FLOP x clock."""
+    return n_sm * 128 * 2 * clock_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND") != "gloo" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(steps=None, seconds=12.0):
+    """Time the FP64 CPU oracle on the bounded sample (cpu_baseline leg)."""
+    import torch
+    import oracle
+    from synth import make_workload, normal_weights
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    torch.set_num_threads(cores)
+    s, spec = make_workload("sio2_192_l2")
+    w = normal_weights(oracle.n_params(spec))
+    oracle.energy_forces_virial(spec, w, s.species, s.pos, s.cell)     # CG tables, warm caches
+    n_done, t0 = 0, time.perf_counter()
+    res = None
+    while True:
+        res = oracle.energy_forces_virial(spec, w, s.species, s.pos, s.cell)
+        n_done += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and n_done >= steps) or (steps is None and el >= seconds):
+            break
+    return dict(value=s.n_atoms * n_done / el, unit=UNIT, cores=torch.get_num_threads(), kind="oracle",
+                sample=f"{n_done} E+F+virial evaluations of a 192-atom SiO2 cell (2.2 g/cm3, same "
+                       f"5-layer model) by the FP64 CPU oracle"), (s, spec, w, res)
+
+
+def traffic_for(kernel, source):
+    """DRAM bytes per launch from a committed ncu capture, if taken on this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        data = json.load(open(path))
+        sha = hashlib.sha256(open(source, "rb").read()).hexdigest()[:16]
+        ent = data.get(kernel)
+        if ent and ent.get("source_sha") == sha:
+            return ent["bytes_per_launch_full_workload"]
+    except Exception:
+        pass
+    return None
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    for _ in range(args.warmup):
+        oracle_sample(steps=1)
+    base, _ = oracle_sample(steps=args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 192.0 / base["value"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "192-atom SiO2 cell, same model"},
+            "cpu_baseline": base, "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                          "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the other precision's line")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default=WORKLOAD)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import numpy as np
+    import torch
+    import paper_2402_03789_gb300 as sn
+    from synth import make_workload, normal_weights
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    s, spec = make_workload(args.workload)
+    weights = normal_weights(sn.n_params(spec))
+    model = sn.SevenNet(spec, weights, device=local)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    species = torch.tensor(s.species, dtype=torch.int32, device=dev)
+    pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
+    off = [0, s.n_atoms]
+    cells = s.cell[None]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    n_edges = len(model.neighbors(s.pos, s.cell)[0])
+
+    def timed(prec):
+        out = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty((s.n_atoms, 3), dtype=torch.float64, device=dev),
+               torch.empty((1, 3, 3), dtype=torch.float64, device=dev))
+        for _ in range(args.warmup):
+            model.evaluate_batch_dev(off, cells, species, pos, prec, stream=stream, out=out)
+        torch.cuda.synchronize(dev)
+        model.profile(True)
+        l0 = sn.SevenNet.launch_count()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        clk = ClockSampler(local)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        clk.start()
+        w0 = time.perf_counter()
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            model.evaluate_batch_dev(off, cells, species, pos, prec, stream=stream, out=out)
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        wall = time.perf_counter() - w0
+        clk.stop()
+        dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+        prof = model.profile_read()
+        model.profile(False)
+        launches = sn.SevenNet.launch_count() - l0
+        dev_ms = max_over_ranks(dev_ms, world, dev)
+        return dev_ms, wall, prof, launches, clk.summary(), out
+
+    dev_ms, wall, prof, launches, clocks, out = timed(args.precision)
+    value = world * s.n_atoms * args.steps / (dev_ms / 1e3)
+    ms_per_step = dev_ms / args.steps
+
+    # e2e: the host-buffer C-ABI call, copies included, every step
+    e2e_t = []
+    model.evaluate(s.pos, s.cell, s.species, args.precision)
+    for _ in range(max(3, args.steps // 2)):
+        t0 = time.perf_counter()
+        model.evaluate(s.pos, s.cell, s.species, args.precision)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_t = max_over_ranks(statistics.median(e2e_t), world, dev)
+    h2d = s.n_atoms * 3 * 8 + s.n_atoms * 4 + 9 * 8
+    d2h = 8 + s.n_atoms * 3 * 8 + 9 * 8
+
+    # roofline of the dominant kernel family (the convolution adjoint)
+    fam = max(("conv_bwd", "conv_fwd"), key=lambda k: prof.get(k, (0, 0))[0])
+    tot_ms, n_launch = prof[fam]
+    flops_step = sum(conv_flops_per_edge(spec, t, fam == "conv_bwd") * n_edges for t in range(spec.n_layers))
+    achieved = flops_step * args.steps / (tot_ms / 1e3) / 1e12
+    peak = fp32_alu_peak_tflops(n_sm, 2070.0)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic_for(fam, os.path.join(ROOT, "paper_2402_03789_gb300", "csrc", "conv.cu")),
+                "kernel": fam, "share_of_step": tot_ms / dev_ms,
+                "peak_source": f"FP32 FFMA: {n_sm} SMs x 128 lanes x 2 FLOP x 2070 MHz (unit counts and max clock)",
+                "flops_per_step": flops_step}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16+f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.workload == WORKLOAD else args.workload,
+                       "n_atoms": s.n_atoms, "n_edges": n_edges, "precision": args.precision,
+                       "model": "5-layer 128x0e+64x1e+32x2e lmax 2, r_c 5 A, MLP 8-64-64 (random FP64 weights)",
+                       "l2": "256 MB buffer zeroed between timed steps", "parallelism": f"replicas x{world}"},
+            "e2e": {"value": world * s.n_atoms / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roofline, "clocks": clocks,
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "wall_ms_per_step": wall * 1e3 / args.steps}
+
+    if not args.no_compare:
+        other = "fp32" if args.precision == "bf16" else "bf16"
+        o_ms, *_ = timed(other)
+        line["compare"] = {other: {"value": world * s.n_atoms * args.steps / (o_ms / 1e3),
+                                   "ms_per_step": o_ms / args.steps}}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        base, (s2, spec2, w2, res) = oracle_sample()
+        line["cpu_baseline"] = base
+        # error of each GPU path on the same 192-atom cell, against the oracle's result
+        Eo, Fo, Wo = res[0], res[1], res[2]
+        m2 = sn.SevenNet(spec2, w2, device=local)
+        errs = {}
+        for prec in ("fp32", "bf16"):
+            E, F, W = m2.evaluate(s2.pos, s2.cell, s2.species, prec)
+            errs[prec] = {"force_rel_rms": float(np.linalg.norm(F - Fo) / np.linalg.norm(Fo)),
+                          "energy_per_atom_ev": abs(E - Eo) / s2.n_atoms,
+                          "virial_rel": float(np.linalg.norm(W - Wo) / np.linalg.norm(Wo))}
+        line["error_vs_oracle_192"] = errs
+        m2.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    model.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

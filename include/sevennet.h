@@ -254,6 +254,20 @@ sevennet_status sevennet_server_poll(sevennet_server* s, uint64_t ticket,
 double sevennet_server_now(const sevennet_server* s);
 void sevennet_server_destroy(sevennet_server* s);
 
+/* Diagnostics (no counterpart in the paper; used for measurement).
+ * sevennet_profile(model, 1) makes every later evaluation on that model record
+ * CUDA events around each kernel family on the stream it runs on
+ * ("neighbors", "linear", "conv_fwd", "conv_bwd", "gate", "other");
+ * sevennet_profile_read() synchronises, adds the recorded intervals up and
+ * returns, per family, the total milliseconds and launches (names: n_max
+ * entries of 32 chars).  Enabling again clears the totals.
+ * sevennet_launch_count() is the number of kernels this library has launched
+ * in the process. */
+sevennet_status sevennet_profile(sevennet_model* model, int32_t enable);
+sevennet_status sevennet_profile_read(sevennet_model* model, int32_t n_max, char* names,
+                                      double* total_ms, int64_t* launches, int32_t* n_out);
+int64_t sevennet_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

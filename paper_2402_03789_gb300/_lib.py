@@ -92,6 +92,9 @@ SIGNATURES = {
     "sevennet_server_poll": (_I32, [_P, ctypes.c_uint64, ctypes.POINTER(Result), ctypes.POINTER(ctypes.c_int)]),
     "sevennet_server_now": (ctypes.c_double, [_P]),
     "sevennet_server_destroy": (None, [_P]),
+    "sevennet_profile": (_I32, [_P, _I32]),
+    "sevennet_profile_read": (_I32, [_P, _I32, ctypes.c_char_p, _D, ctypes.POINTER(_I64), _IP]),
+    "sevennet_launch_count": (_I64, []),
 }
 
 _lib = None

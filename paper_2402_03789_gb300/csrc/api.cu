@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 namespace sn {
@@ -36,6 +37,38 @@ int num_sms(int device) {
         cached[device] = v;
     }
     return cached[device];
+}
+
+// ---------------------------------------------------------------- diagnostics
+static std::atomic<int64_t> g_launch_count{0};
+
+void count_launches(int n) { g_launch_count += n; }
+
+cudaEvent_t Profiler::get() {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(Profiler* p, int fam, cudaStream_t st, cudaEvent_t* a) {
+    (void)fam;
+    *a = nullptr;
+    if (!p || !p->on) return;
+    *a = p->get();
+    cudaEventRecord(*a, st);
+}
+
+void prof_end(Profiler* p, int fam, cudaStream_t st, cudaEvent_t a, int n_launches) {
+    if (!p || !p->on || !a) return;
+    cudaEvent_t b = p->get();
+    cudaEventRecord(b, st);
+    p->pending.push_back({fam, a, b});
+    p->launches[fam] += n_launches;
 }
 
 // ---------------------------------------------------------------- layer specs
@@ -291,7 +324,19 @@ sevennet_status run_model(sevennet_model* M, Workspace* ws, const BatchHost& b, 
     const int64_t N = b.atom_off[b.n_structs];
     const int T = M->T;
     const int mul0 = M->cfg.mul[0];
+    Profiler* P = &M->prof;
+    cudaEvent_t ev;
+    auto gemm = [&](const GemmBatch& g) {
+        if (!g.n) return;
+        prof_begin(P, PF_LINEAR, st, &ev);
+        launch_gemm(g, prec, st);
+        prof_end(P, PF_LINEAR, st, ev, 1);
+        count_launches(1);
+    };
+    prof_begin(P, PF_OTHER, st, &ev);
     launch_embed(M->embed, ws->species_s, N, mul0, M->cfg.n_species, ws->h, st);
+    prof_end(P, PF_OTHER, st, ev, 1);
+    count_launches(1);
     for (int t = 0; t < T; ++t) {
         const LayerDev& L = M->layers[t];
         float* x = ws->xs + (size_t)t * N * M->x_max;
@@ -305,36 +350,51 @@ sevennet_status run_model(sevennet_model* M, Workspace* ws, const BatchHost& b, 
                 g.p[g.n++] = GemmProb{ws->h, L.sc[l], L.sch[l], y, N, 2 * l + 1, L.in_mul[l], L.y_mul[l],
                                       L.h_in_dim, L.in_off[l], L.y_dim, L.y_off[l], 0};
         }
-        launch_gemm(g, prec, st);
+        gemm(g);
+        prof_begin(P, PF_CONV_FWD, st, &ev);
         launch_conv_fwd(L, M->H, prec, N, E, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m, st);
+        prof_end(P, PF_CONV_FWD, st, ev, 1);
+        count_launches(1);
         GemmBatch g2{};
         for (int l = 0; l < 3; ++l) {
             if (!L.y_mul[l] || !L.msg_mul[l]) continue;
             g2.p[g2.n++] = GemmProb{ws->m, L.lin2[l], L.lin2h[l], y, N, 2 * l + 1, L.msg_mul[l], L.y_mul[l],
                                     L.m_dim, L.msg_off[l], L.y_dim, L.y_off[l], L.in_mul[l] ? 1 : 0};
         }
-        launch_gemm(g2, prec, st);
+        gemm(g2);
+        prof_begin(P, PF_GATE, st, &ev);
         launch_gate_fwd(L, mul0, M->cfg.mul, M->lmax, N, y, ws->h, st);
+        prof_end(P, PF_GATE, st, ev, 1);
+        count_launches(1);
     }
+    prof_begin(P, PF_OTHER, st, &ev);
     launch_readout(ws->h, M->layers[T - 1].h_out_dim, M->readout, M->shift_dev, ws->species_s, N, mul0,
                    M->cfg.n_species, ws->e_atom, st);
+    prof_end(P, PF_OTHER, st, ev, 1);
+    count_launches(1);
     // reverse path
     if (E > 0) SN_CUDA(cudaMemsetAsync(ws->gd, 0, (size_t)E * 3 * sizeof(float), st));
     for (int t = T - 1; t >= 0; --t) {
         const LayerDev& L = M->layers[t];
         float* x = ws->xs + (size_t)t * N * M->x_max;
         float* y = ws->ys + (size_t)t * N * M->y_max;
+        prof_begin(P, PF_GATE, st, &ev);
         launch_gate_bwd(L, mul0, M->cfg.mul, M->lmax, N, y, ws->gh, M->readout, ws->gy, st);
+        prof_end(P, PF_GATE, st, ev, 1);
+        count_launches(1);
         GemmBatch g{};
         for (int l = 0; l < 3; ++l) {
             if (!L.y_mul[l] || !L.msg_mul[l]) continue;
             g.p[g.n++] = GemmProb{ws->gy, L.lin2T[l], L.lin2Th[l], ws->m, N, 2 * l + 1, L.y_mul[l], L.msg_mul[l],
                                   L.y_dim, L.y_off[l], L.m_dim, L.msg_off[l], 0};
         }
-        launch_gemm(g, prec, st);
+        gemm(g);
         SN_CUDA(cudaMemsetAsync(ws->gx, 0, (size_t)N * L.x_dim * sizeof(float), st));
+        prof_begin(P, PF_CONV_BWD, st, &ev);
         launch_conv_bwd(L, M->H, prec, N, E, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m, ws->gx,
                         ws->gd, st);
+        prof_end(P, PF_CONV_BWD, st, ev, 1);
+        count_launches(1);
         if (t == 0) break;
         GemmBatch a{}, c{};
         for (int l = 0; l < 3; ++l) {
@@ -345,12 +405,15 @@ sevennet_status run_model(sevennet_model* M, Workspace* ws, const BatchHost& b, 
                 c.p[c.n++] = GemmProb{ws->gy, L.scT[l], L.scTh[l], ws->gh, N, 2 * l + 1, L.y_mul[l], L.in_mul[l],
                                       L.y_dim, L.y_off[l], L.h_in_dim, L.in_off[l], 1};
         }
-        launch_gemm(a, prec, st);
-        launch_gemm(c, prec, st);
+        gemm(a);
+        gemm(c);
     }
+    prof_begin(P, PF_OTHER, st, &ev);
     launch_forces(N, ws->row_ptr, ws->rev, ws->gd, ws->geom, ws->f_s, ws->w_atom, st);
     launch_reduce_structs(b.n_structs, ws->atom_off, ws->e_atom, ws->w_atom, energy_dev, virial_dev, st);
     launch_scatter_forces(N, ws->perm, ws->f_s, forces_dev, st);
+    prof_end(P, PF_OTHER, st, ev, 3);
+    count_launches(3);
     SN_CUDA(cudaGetLastError());
     return SEVENNET_OK;
 }
@@ -606,7 +669,11 @@ sevennet_status eval_batch(sevennet_model* M, Workspace* ws, const BatchHost& b,
     SN_CHECK(prec == SEVENNET_FP32 || prec == SEVENNET_BF16, SEVENNET_EINVAL, "unknown precision");
     const int64_t N = b.atom_off[b.n_structs];
     int64_t E = 0;
+    cudaEvent_t ev;
+    prof_begin(&M->prof, PF_NEIGHBORS, st, &ev);
     SN_TRY(build_neighbors(M, ws, b, pos_dev, species_dev, st, &E));
+    prof_end(&M->prof, PF_NEIGHBORS, st, ev, 9);
+    count_launches(10);
     if (N > 0) {
         check_species_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, species_dev, M->cfg.n_species,
                                                                           ws->flags);
@@ -810,5 +877,51 @@ sevennet_status sevennet_conv_backward_dev(sevennet_model* M, int32_t layer, int
     cudaFreeAsync(geom, st);
     return SEVENNET_OK;
 }
+
+}  // extern "C"
+
+extern "C" {
+
+sevennet_status sevennet_profile(sevennet_model* M, int32_t enable) {
+    SN_CHECK(M, SEVENNET_EINVAL, "NULL model");
+    SN_CUDA(cudaSetDevice(M->device));
+    Profiler& p = M->prof;
+    for (auto& r : p.pending) {
+        cudaEventSynchronize(r.b);
+        p.pool.push_back(r.a);
+        p.pool.push_back(r.b);
+    }
+    p.pending.clear();
+    for (int i = 0; i < PF_COUNT; ++i) { p.total_ms[i] = 0; p.launches[i] = 0; }
+    p.on = enable != 0;
+    return SEVENNET_OK;
+}
+
+sevennet_status sevennet_profile_read(sevennet_model* M, int32_t n_max, char* names, double* total_ms,
+                                      int64_t* launches, int32_t* n_out) {
+    SN_CHECK(M, SEVENNET_EINVAL, "NULL model");
+    SN_CUDA(cudaSetDevice(M->device));
+    Profiler& p = M->prof;
+    for (auto& r : p.pending) {
+        SN_CUDA(cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        SN_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        p.total_ms[r.fam] += ms;
+        p.pool.push_back(r.a);
+        p.pool.push_back(r.b);
+    }
+    p.pending.clear();
+    static const char* fam[PF_COUNT] = {"neighbors", "linear", "conv_fwd", "conv_bwd", "gate", "other"};
+    const int n = std::min<int>(n_max, PF_COUNT);
+    for (int i = 0; i < n; ++i) {
+        if (names) { std::memset(names + 32 * i, 0, 32); std::strncpy(names + 32 * i, fam[i], 31); }
+        if (total_ms) total_ms[i] = p.total_ms[i];
+        if (launches) launches[i] = p.launches[i];
+    }
+    if (n_out) *n_out = n;
+    return SEVENNET_OK;
+}
+
+int64_t sevennet_launch_count(void) { return g_launch_count.load(); }
 
 }  // extern "C"

@@ -138,6 +138,21 @@ struct LayerDev {
 
 struct Workspace;
 
+// Kernel-family timing with CUDA events (diagnostics).
+enum ProfFamily { PF_NEIGHBORS = 0, PF_LINEAR, PF_CONV_FWD, PF_CONV_BWD, PF_GATE, PF_OTHER, PF_COUNT };
+struct Profiler {
+    bool on = false;
+    struct Rec { int fam; cudaEvent_t a, b; };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    double total_ms[PF_COUNT] = {0};
+    int64_t launches[PF_COUNT] = {0};
+    cudaEvent_t get();
+};
+void prof_begin(Profiler* p, int fam, cudaStream_t st, cudaEvent_t* a);
+void prof_end(Profiler* p, int fam, cudaStream_t st, cudaEvent_t a, int n_launches);
+void count_launches(int n);
+
 }  // namespace sn
 
 struct sevennet_model {
@@ -152,6 +167,7 @@ struct sevennet_model {
     double* shift_dev = nullptr;
     cudaStream_t stream = nullptr;
     sn::Workspace* ws = nullptr;
+    sn::Profiler prof;
     std::vector<void*> allocations;
 };
 

@@ -122,6 +122,30 @@ class SevenNet:
             self.lib.sevennet_nlist_destroy(h)
         return dst, src, sh
 
+    # -------------------------------------------------------------- diagnostics
+    def profile(self, enable=True):
+        L.check(self.lib.sevennet_profile(self.handle, 1 if enable else 0))
+
+    def profile_read(self):
+        """{family: (total_ms, launches)} since profile(True)."""
+        n = 8
+        names = ctypes.create_string_buffer(32 * n)
+        ms = np.zeros(n)
+        cnt = np.zeros(n, np.int64)
+        nout = ctypes.c_int32()
+        L.check(self.lib.sevennet_profile_read(self.handle, n, names, L.dptr(ms),
+                                               cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                               ctypes.byref(nout)))
+        out = {}
+        for i in range(nout.value):
+            nm = names.raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
+            out[nm] = (float(ms[i]), int(cnt[i]))
+        return out
+
+    @staticmethod
+    def launch_count():
+        return int(L.load().sevennet_launch_count())
+
     # -------------------------------------------------------------- device API
     def evaluate_batch_dev(self, atom_offsets, cells, species, pos, precision="fp32", pbc=None,
                            stream=None, out=None):
