@@ -158,7 +158,7 @@ sevennet_status sevennet_eval_energy_forces_virial(sevennet_model* model, int64_
                                                    double* forces, double* virial);
 
 /* Batched evaluation on device buffers, stream-ordered on `stream`
- * (a cudaStream_t; NULL = the model's own stream).  n_structs independent
+ * (a cudaStream_t; NULL = the CUDA default stream, as everywhere in CUDA).  n_structs independent
  * periodic cells; structure s owns atoms [atom_offsets[s], atom_offsets[s+1]).
  * Host arrays: atom_offsets [n_structs+1], cells [n_structs][3][3],
  * pbc [n_structs][3] (NULL = all periodic).  Device arrays: species [N],
@@ -182,7 +182,9 @@ sevennet_status sevennet_eval_batch_dev(sevennet_model* model, int32_t n_structs
  *     [l][m][channel] blocks; m_out [n_atoms][m_dim] FP32 messages, paths
  *     concatenated per l3 in path order.
  * Backward: given g_m, writes g_x (overwritten) and adds dE/dd into g_d
- * (accumulated; zero it first).  prec selects the radial-MLP arithmetic. */
+ * (accumulated; zero it first).  prec selects the radial-MLP arithmetic.
+ * Both are ordered on `stream` (NULL = the CUDA default stream) and return
+ * without synchronising. */
 sevennet_status sevennet_conv_forward_dev(sevennet_model* model, int32_t layer,
                                           int64_t n_atoms, int64_t n_edges,
                                           const int32_t* row_ptr, const int32_t* src,
@@ -234,6 +236,7 @@ typedef struct {
     double* forces;           /* caller buffer [n_atoms][3], filled by poll */
     double  virial[9];        /* eV */
     double  submit_s;         /* seconds on the server clock */
+    double  start_s;          /* when its batch was launched */
     double  done_s;
     int32_t batch_id;         /* batch the request ran in */
     int32_t batch_structs;    /* structures in that batch */

@@ -54,6 +54,7 @@ class Result(ctypes.Structure):
         ("forces", ctypes.POINTER(ctypes.c_double)),
         ("virial", ctypes.c_double * 9),
         ("submit_s", ctypes.c_double),
+        ("start_s", ctypes.c_double),
         ("done_s", ctypes.c_double),
         ("batch_id", ctypes.c_int32),
         ("batch_structs", ctypes.c_int32),

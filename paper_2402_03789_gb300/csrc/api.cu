@@ -449,7 +449,7 @@ sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const do
     int ndev = 0;
     SN_CUDA(cudaGetDeviceCount(&ndev));
     SN_CHECK(device >= 0 && device < ndev, SEVENNET_EINVAL, "device %d out of range (%d devices)", device, ndev);
-    SN_CUDA(cudaSetDevice(device));
+    SN_ENTER(device);
     int major = 0, minor = 0;
     SN_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device));
     SN_CUDA(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device));
@@ -597,6 +597,8 @@ sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const do
             auto w2T = scaled(weights + e2->off, H, D.W, s2, true);
             if ((s = dev_upload(M, w0, &L.mlp0))) return fail(s);
             if ((s = dev_upload(M, w1, &L.mlp1))) return fail(s);
+            auto w1T = scaled(weights + e1->off, H, H, 1.0 / std::sqrt((double)H), true);
+            if ((s = dev_upload(M, w1T, &L.mlp1T))) return fail(s);
             if ((s = dev_upload(M, w2, &L.mlp2))) return fail(s);
             if ((s = dev_upload(M, w2T, &L.mlp2T))) return fail(s);
             if ((s = dev_upload(M, to_bf16(w2T), &L.mlp2h))) return fail(s);   // [W][H]
@@ -696,7 +698,7 @@ sevennet_status sevennet_build_neighbors(sevennet_model* M, int64_t n_atoms, con
     SN_CHECK(M && out && n_edges && cell && (pos || n_atoms == 0), SEVENNET_EINVAL, "NULL argument");
     SN_CHECK(n_atoms >= 0, SEVENNET_EINVAL, "n_atoms < 0");
     *out = nullptr;
-    SN_CUDA(cudaSetDevice(M->device));
+    SN_ENTER(M->device);
     BatchHost b;
     b.n_structs = 1;
     b.atom_off = {0, n_atoms};
@@ -749,7 +751,7 @@ sevennet_status sevennet_build_neighbors(sevennet_model* M, int64_t n_atoms, con
 
 sevennet_status sevennet_nlist_export(const sevennet_nlist* nl, int32_t* dst, int32_t* src, int32_t* shift) {
     SN_CHECK(nl, SEVENNET_EINVAL, "NULL list");
-    SN_CUDA(cudaSetDevice(nl->device));
+    SN_ENTER(nl->device);
     if (nl->n_edges == 0) return SEVENNET_OK;
     if (dst) SN_CUDA(cudaMemcpy(dst, nl->dst, nl->n_edges * sizeof(int), cudaMemcpyDeviceToHost));
     if (src) SN_CUDA(cudaMemcpy(src, nl->src, nl->n_edges * sizeof(int), cudaMemcpyDeviceToHost));
@@ -772,7 +774,7 @@ sevennet_status sevennet_eval_energy_forces_virial(sevennet_model* M, int64_t n_
                                                    double* virial) {
     SN_CHECK(M && cell && (n_atoms == 0 || (pos && species)), SEVENNET_EINVAL, "NULL argument");
     SN_CHECK(n_atoms >= 0, SEVENNET_EINVAL, "n_atoms < 0");
-    SN_CUDA(cudaSetDevice(M->device));
+    SN_ENTER(M->device);
     for (int64_t i = 0; i < 3 * n_atoms; ++i) SN_CHECK(std::isfinite(pos[i]), SEVENNET_EINVAL, "position not finite");
     for (int64_t i = 0; i < n_atoms; ++i)
         SN_CHECK(species[i] >= 0 && species[i] < M->cfg.n_species, SEVENNET_EINVAL, "species index out of range");
@@ -817,14 +819,14 @@ sevennet_status sevennet_eval_batch_dev(sevennet_model* M, int32_t n_structs, co
                                         const double* pos_dev, sevennet_precision prec, double* energy_dev,
                                         double* forces_dev, double* virial_dev, void* stream) {
     SN_CHECK(M && atom_offsets && cells && n_structs >= 1, SEVENNET_EINVAL, "bad argument");
-    SN_CUDA(cudaSetDevice(M->device));
+    SN_ENTER(M->device);
     BatchHost b;
     b.n_structs = n_structs;
     b.atom_off.assign(atom_offsets, atom_offsets + n_structs + 1);
     b.cells.assign(cells, cells + (size_t)n_structs * 9);
     if (pbc) b.pbc.assign(pbc, pbc + (size_t)n_structs * 3);
     SN_CHECK(b.atom_off[n_structs] == 0 || (species_dev && pos_dev), SEVENNET_EINVAL, "NULL device array");
-    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : M->stream;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);   // NULL: the CUDA default stream
     return eval_batch(M, M->ws, b, species_dev, pos_dev, prec, energy_dev, forces_dev, virial_dev, st);
 }
 
@@ -840,8 +842,8 @@ sevennet_status sevennet_conv_forward_dev(sevennet_model* M, int32_t layer, int6
                                           const float* x, float* m_out, sevennet_precision prec, void* stream) {
     SN_CHECK(M && layer >= 0 && layer < M->T && n_atoms >= 0 && n_edges >= 0, SEVENNET_EINVAL, "bad argument");
     SN_CHECK(row_ptr && x && m_out && (n_edges == 0 || (src && d)), SEVENNET_EINVAL, "NULL argument");
-    SN_CUDA(cudaSetDevice(M->device));
-    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : M->stream;
+    SN_ENTER(M->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);   // NULL: the CUDA default stream
     // build (dst, float4 geometry) from the caller's CSR + FP32 displacements
     int* dst = nullptr;
     float4* geom = nullptr;
@@ -862,8 +864,8 @@ sevennet_status sevennet_conv_backward_dev(sevennet_model* M, int32_t layer, int
                                            sevennet_precision prec, void* stream) {
     SN_CHECK(M && layer >= 0 && layer < M->T && n_atoms >= 0 && n_edges >= 0, SEVENNET_EINVAL, "bad argument");
     SN_CHECK(row_ptr && x && g_m && g_x && (n_edges == 0 || (src && d && g_d)), SEVENNET_EINVAL, "NULL argument");
-    SN_CUDA(cudaSetDevice(M->device));
-    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : M->stream;
+    SN_ENTER(M->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);   // NULL: the CUDA default stream
     int* dst = nullptr;
     float4* geom = nullptr;
     const size_t e1 = std::max<int64_t>(n_edges, 1);
@@ -884,7 +886,7 @@ extern "C" {
 
 sevennet_status sevennet_profile(sevennet_model* M, int32_t enable) {
     SN_CHECK(M, SEVENNET_EINVAL, "NULL model");
-    SN_CUDA(cudaSetDevice(M->device));
+    SN_ENTER(M->device);
     Profiler& p = M->prof;
     for (auto& r : p.pending) {
         cudaEventSynchronize(r.b);
@@ -900,7 +902,7 @@ sevennet_status sevennet_profile(sevennet_model* M, int32_t enable) {
 sevennet_status sevennet_profile_read(sevennet_model* M, int32_t n_max, char* names, double* total_ms,
                                       int64_t* launches, int32_t* n_out) {
     SN_CHECK(M, SEVENNET_EINVAL, "NULL model");
-    SN_CUDA(cudaSetDevice(M->device));
+    SN_ENTER(M->device);
     Profiler& p = M->prof;
     for (auto& r : p.pending) {
         SN_CUDA(cudaEventSynchronize(r.b));

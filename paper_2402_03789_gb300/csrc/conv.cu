@@ -24,8 +24,8 @@
 
 namespace sn {
 
-constexpr int KS = 16;        // k-slice of the W3 staging in phase D
-constexpr int DCOLS = 512;    // columns per pass of phase D (32 lanes x 4 quads x 4)
+constexpr int KS = 8;         // k-slice of the W3 staging in phase D
+constexpr int DCOLS = 512;    // columns per pass of phase D
 constexpr int CS = 32;        // column slice of phase F (adjoint W3 product)
 
 struct ConvSmem {
@@ -149,15 +149,17 @@ __device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem
         }
     }
     __syncthreads();
-    // B: A1 = B @ W1, A2 = silu(A1) @ W2   (layouts [H][EC])
+    // B: A1 = B @ W1 (layout [H][EC]); H1 = silu(A1) lives in the staging area until phase D
     float* s_A1 = smem + L.A1;
     float* s_A2 = smem + L.A2;
     float* s_H2 = smem + L.H2;
+    float* s_H1 = smem + L.stage;
     for (int i = t; i < H * EC; i += CONV_THREADS) {
         const int j = i / EC, e = i % EC;
         float a = 0.0f;
         for (int n = 0; n < D.n_basis; ++n) a = fmaf(s_B[n * EC + e], __ldg(W1 + n * H + j), a);
         s_A1[i] = a;
+        s_H1[i] = siluf_(a);
     }
     // C: G matrices (independent of B)
     float* s_G = smem + L.G;
@@ -166,13 +168,26 @@ __device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem
         path_G(D.paths[p].kind, s_Y + e * 9, s_G + e * D.nG + D.paths[p].g_off);
     }
     __syncthreads();
-    for (int i = t; i < H * EC; i += CONV_THREADS) {
-        const int j = i / EC, e = i % EC;
-        float a = 0.0f;
+    // A2 = H1 @ W2, H2 = silu(A2): each thread computes 4 hidden units of one edge
+    for (int idx = t; idx < (H / 4) * EC; idx += CONV_THREADS) {
+        const int jq = idx / EC, e = idx % EC;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll 8
-        for (int k = 0; k < H; ++k) a = fmaf(siluf_(s_A1[k * EC + e]), __ldg(W2 + k * H + j), a);
-        s_A2[i] = a;
-        s_H2[i] = siluf_(a);
+        for (int k = 0; k < H; ++k) {
+            const float4 b = __ldg(reinterpret_cast<const float4*>(W2 + k * H) + jq);
+            const float a = s_H1[k * EC + e];
+            a0 = fmaf(a, b.x, a0);
+            a1 = fmaf(a, b.y, a1);
+            a2 = fmaf(a, b.z, a2);
+            a3 = fmaf(a, b.w, a3);
+        }
+        const float av[4] = {a0, a1, a2, a3};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int o = (4 * jq + q) * EC + e;
+            s_A2[o] = av[q];
+            s_H2[o] = siluf_(av[q]);
+        }
     }
     __syncthreads();
 }
@@ -181,17 +196,21 @@ __device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem
 template <int H>
 __device__ __forceinline__ void chunk_w_gemm_f32(const ConvDesc& D, const ConvSmem& L, float* smem,
                                                  const float* __restrict__ W3) {
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int NEG = EC / 4;                 // groups of 4 edges
+    constexpr int NCG = CONV_THREADS / NEG;     // column-quad threads per edge group
+    constexpr int NQ = DCOLS / (4 * NCG);       // column quads per thread and pass
+    const int t = threadIdx.x;
+    const int eg = t / NCG, cg = t % NCG;
     const float* s_H2 = smem + L.H2;
     float4* st4 = reinterpret_cast<float4*>(smem + L.stage);   // [KS][DCOLS/4]
     float* s_w = smem + L.w;
     const int W = D.W;
     for (int cb = 0; cb < W; cb += DCOLS) {
-        float acc[4][4][4];
+        float acc[4][NQ][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+            for (int j = 0; j < NQ; ++j)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
         for (int k0 = 0; k0 < H; k0 += KS) {
@@ -204,13 +223,13 @@ __device__ __forceinline__ void chunk_w_gemm_f32(const ConvDesc& D, const ConvSm
                 st4[i] = v;
             }
             __syncthreads();
-#pragma unroll 4
+#pragma unroll
             for (int kk = 0; kk < KS; ++kk) {
-                const float4 a = *reinterpret_cast<const float4*>(s_H2 + (k0 + kk) * EC + 4 * warp);
+                const float4 a = *reinterpret_cast<const float4*>(s_H2 + (k0 + kk) * EC + 4 * eg);
                 const float av[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float4 b = st4[kk * (DCOLS / 4) + lane + 32 * j];
+                for (int j = 0; j < NQ; ++j) {
+                    const float4 b = st4[kk * (DCOLS / 4) + cg + NCG * j];
                     const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
@@ -220,14 +239,164 @@ __device__ __forceinline__ void chunk_w_gemm_f32(const ConvDesc& D, const ConvSm
             }
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int col = cb + 4 * (lane + 32 * j);
+        for (int j = 0; j < NQ; ++j) {
+            const int col = cb + 4 * (cg + NCG * j);
             if (col < W) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
-                    *reinterpret_cast<float4*>(s_w + (4 * warp + i) * D.Wpad + col) =
+                    *reinterpret_cast<float4*>(s_w + (4 * eg + i) * D.Wpad + col) =
                         make_float4(acc[i][j][0], acc[i][j][1], acc[i][j][2], acc[i][j][3]);
             }
+        }
+    }
+    __syncthreads();
+}
+
+// ---- BF16 tensor-core variants of phases D and F (mma.sync m16n8k16, FP32 accumulate)
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// Activations enter the tensor cores as hi + lo BF16 pairs (two MMAs), weights as
+// one BF16 value: the product keeps ~16 mantissa bits of the activation.
+constexpr bool SPLIT_ACT = true;
+
+__device__ __forceinline__ void split_bf16(float x, float y, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x - hf.x, y - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Phase D (BF16): w[e][c] = sum_k H2[k][e] W3[k][c]; B operand W3T [W][H] (bf16).
+template <int H>
+__device__ __forceinline__ void chunk_w_gemm_bf16(const ConvDesc& D, const ConvSmem& L, float* smem,
+                                                  const __nv_bfloat16* __restrict__ W3T) {
+    constexpr int KSN = H / 16;
+    constexpr int MT = EC / 16;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tq = lane & 3;
+    const float* s_H2 = smem + L.H2;
+    float* s_w = smem + L.w;
+    uint32_t af[MT][KSN][4], al[MT][KSN][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int ks = 0; ks < KSN; ++ks) {
+            const int k0 = ks * 16 + 2 * tq, e0 = mt * 16 + g;
+            split_bf16(s_H2[k0 * EC + e0], s_H2[(k0 + 1) * EC + e0], af[mt][ks][0], al[mt][ks][0]);
+            split_bf16(s_H2[k0 * EC + e0 + 8], s_H2[(k0 + 1) * EC + e0 + 8], af[mt][ks][1], al[mt][ks][1]);
+            split_bf16(s_H2[(k0 + 8) * EC + e0], s_H2[(k0 + 9) * EC + e0], af[mt][ks][2], al[mt][ks][2]);
+            split_bf16(s_H2[(k0 + 8) * EC + e0 + 8], s_H2[(k0 + 9) * EC + e0 + 8], af[mt][ks][3], al[mt][ks][3]);
+        }
+    const int ntiles = D.W / 8;
+    uint32_t bn[KSN][2];
+    auto loadb = [&](int nt, uint32_t (*b)[2]) {
+        const uint32_t* row = reinterpret_cast<const uint32_t*>(W3T + (size_t)(nt * 8 + g) * H);
+#pragma unroll
+        for (int ks = 0; ks < KSN; ++ks) {
+            b[ks][0] = __ldg(row + ks * 8 + tq);
+            b[ks][1] = __ldg(row + ks * 8 + 4 + tq);
+        }
+    };
+    if (warp < ntiles) loadb(warp, bn);
+    for (int nt = warp; nt < ntiles; nt += CONV_WARPS) {
+        uint32_t bc[KSN][2];
+#pragma unroll
+        for (int ks = 0; ks < KSN; ++ks) { bc[ks][0] = bn[ks][0]; bc[ks][1] = bn[ks][1]; }
+        if (nt + CONV_WARPS < ntiles) loadb(nt + CONV_WARPS, bn);
+        float c[MT][4];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) c[mt][0] = c[mt][1] = c[mt][2] = c[mt][3] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < KSN; ++ks)
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                mma_bf16(c[mt], af[mt][ks], bc[ks]);
+                if constexpr (SPLIT_ACT) mma_bf16(c[mt], al[mt][ks], bc[ks]);
+            }
+        const int col = nt * 8 + 2 * tq;
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            const int r = mt * 16 + g;
+            *reinterpret_cast<float2*>(s_w + r * D.Wpad + col) = make_float2(c[mt][0], c[mt][1]);
+            *reinterpret_cast<float2*>(s_w + (r + 8) * D.Wpad + col) = make_float2(c[mt][2], c[mt][3]);
+        }
+    }
+    __syncthreads();
+}
+
+// Phase F (BF16): gH2[k][e] = sum_c gw[e][c] W3[k][c]; B operand W3 [H][W] (bf16).
+template <int H>
+__device__ __forceinline__ void chunk_gw_gemm_bf16(const ConvDesc& D, const ConvSmem& L, float* smem,
+                                                   const __nv_bfloat16* __restrict__ W3h) {
+    constexpr int NT = H / 8;                  // n tiles of 8 hidden units
+    constexpr int KSPLIT = CONV_WARPS / NT;    // warps sharing one n tile split K
+    constexpr int MT = EC / 16;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tq = lane & 3;
+    const int nt = warp % NT, kp = warp / NT;
+    const float* s_w = smem + L.w;
+    const int W = D.W;
+    __syncthreads();
+    float c[MT][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) c[mt][0] = c[mt][1] = c[mt][2] = c[mt][3] = 0.f;
+    const uint32_t* brow = reinterpret_cast<const uint32_t*>(W3h + (size_t)(nt * 8 + g) * W);
+    for (int ks = kp; ks < W / 16; ks += KSPLIT) {
+        const int c0 = ks * 16 + 2 * tq;
+        uint32_t b[2] = {__ldg(brow + (c0 >> 1)), __ldg(brow + ((c0 + 8) >> 1))};
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            const int e = mt * 16 + g;
+            const float2 x0 = *reinterpret_cast<const float2*>(s_w + e * D.Wpad + c0);
+            const float2 x1 = *reinterpret_cast<const float2*>(s_w + (e + 8) * D.Wpad + c0);
+            const float2 x2 = *reinterpret_cast<const float2*>(s_w + e * D.Wpad + c0 + 8);
+            const float2 x3 = *reinterpret_cast<const float2*>(s_w + (e + 8) * D.Wpad + c0 + 8);
+            uint32_t a[4], al[4];
+            split_bf16(x0.x, x0.y, a[0], al[0]);
+            split_bf16(x1.x, x1.y, a[1], al[1]);
+            split_bf16(x2.x, x2.y, a[2], al[2]);
+            split_bf16(x3.x, x3.y, a[3], al[3]);
+            mma_bf16(c[mt], a, b);
+            if constexpr (SPLIT_ACT) mma_bf16(c[mt], al, b);
+        }
+    }
+    float* s_gH = smem + L.gH;                 // [H][EC]
+    float* red = smem + L.stage;               // [KSPLIT-1][8 warps' tiles]
+    const int k = nt * 8 + 2 * tq;
+    if (KSPLIT > 1) {
+        if (kp > 0) {
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) red[((kp - 1) * NT + nt) * 256 + (mt * 4 + q) * 32 + lane] = c[mt][q];
+        }
+        __syncthreads();
+        if (kp == 0) {
+            for (int j = 1; j < KSPLIT; ++j)
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) c[mt][q] += red[((j - 1) * NT + nt) * 256 + (mt * 4 + q) * 32 + lane];
+        }
+    }
+    if (kp == 0) {
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            const int e = mt * 16 + g;
+            s_gH[k * EC + e] = c[mt][0];
+            s_gH[(k + 1) * EC + e] = c[mt][1];
+            s_gH[k * EC + e + 8] = c[mt][2];
+            s_gH[(k + 1) * EC + e + 8] = c[mt][3];
         }
     }
     __syncthreads();
@@ -282,35 +451,46 @@ __device__ __forceinline__ void tp_fwd_group(const PathDesc& P, int u, int c0, i
             for (int c = 0; c < N3; ++c) mp[c * P.m_mul] += acc[c];
         }
     };
-    for (int e = 0; e < ne; ++e) {
-        const int v = s_dst[e];
-        if (v != cur) {
-            if (cur >= 0) flush(cur);
-            cur = v;
+    constexpr int PF = 4;       // edges whose gathers are in flight together
+    for (int e0 = 0; e0 < ne; e0 += PF) {
+        float xv[PF][N1];
 #pragma unroll
-            for (int c = 0; c < N3; ++c) acc[c] = 0.0f;
+        for (int q = 0; q < PF; ++q) {
+            const int e = min(e0 + q, ne - 1);
+            const float* xr = xb + (size_t)s_src[e] * x_dim;
+#pragma unroll
+            for (int a = 0; a < N1; ++a) xv[q][a] = __ldg(xr + a * P.mul);
         }
-        const float wv = s_w[e * Wpad + col];
-        const float* xr = xb + (size_t)s_src[e] * x_dim;
-        float xv[N1];
 #pragma unroll
-        for (int a = 0; a < N1; ++a) xv[a] = __ldg(xr + a * P.mul);
-        const float* G = s_G + e * nG + P.g_off;
+        for (int q = 0; q < PF; ++q) {
+            const int e = e0 + q;
+            if (e >= ne) break;
+            const int v = s_dst[e];
+            if (v != cur) {
+                if (cur >= 0) flush(cur);
+                cur = v;
 #pragma unroll
-        for (int c = 0; c < N3; ++c) {
-            float tt = 0.0f;
+                for (int c = 0; c < N3; ++c) acc[c] = 0.0f;
+            }
+            const float wv = s_w[e * Wpad + col];
+            const float* G = s_G + e * nG + P.g_off;
 #pragma unroll
-            for (int a = 0; a < N1; ++a) tt = fmaf(xv[a], G[a * N3 + c], tt);
-            acc[c] = fmaf(wv, tt, acc[c]);
+            for (int c = 0; c < N3; ++c) {
+                float tt = 0.0f;
+#pragma unroll
+                for (int a = 0; a < N1; ++a) tt = fmaf(xv[q][a], G[a * N3 + c], tt);
+                acc[c] = fmaf(wv, tt, acc[c]);
+            }
         }
     }
     if (cur >= 0) flush(cur);
 }
 
-template <int H>
-__global__ void __launch_bounds__(CONV_THREADS, 1)
+template <int H, bool BF>
+__global__ void __launch_bounds__(CONV_THREADS, 2)
 conv_fwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __restrict__ W2,
-                const float* __restrict__ W3, int n_atoms, int n_edges,
+                const float* __restrict__ W3, const __nv_bfloat16* __restrict__ W3T_h,
+                int n_atoms, int n_edges,
                 const int* __restrict__ row_ptr, const int* __restrict__ dst,
                 const int* __restrict__ src, const float4* __restrict__ geom,
                 const float* __restrict__ x, float* __restrict__ m) {
@@ -334,7 +514,8 @@ conv_fwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
         const int ne = min(EC, E1 - c0);
         __syncthreads();
         chunk_prologue<H>(D, L, smem, c0, ne, dst, src, geom, W1, W2);
-        chunk_w_gemm_f32<H>(D, L, smem, W3);
+        if constexpr (BF) chunk_w_gemm_bf16<H>(D, L, smem, W3T_h);
+        else chunk_w_gemm_f32<H>(D, L, smem, W3);
         for (int s = 0; s < D.n_slots[warp]; ++s) {
             const int g = D.slot_group[warp][s];
             const PathDesc& P = D.paths[g >> 8];
@@ -489,10 +670,12 @@ __device__ __forceinline__ void chunk_gw_gemm_f32(const ConvDesc& D, const ConvS
     __syncthreads();
 }
 
-template <int H>
-__global__ void __launch_bounds__(CONV_THREADS, 1)
+template <int H, bool BF>
+__global__ void __launch_bounds__(CONV_THREADS, 2)
 conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __restrict__ W2,
-                const float* __restrict__ W3, const float* __restrict__ W3T, int n_atoms,
+                const float* __restrict__ W2T, const float* __restrict__ W3, const float* __restrict__ W3T,
+                const __nv_bfloat16* __restrict__ W3T_h, const __nv_bfloat16* __restrict__ W3_h,
+                int n_atoms,
                 int n_edges, const int* __restrict__ row_ptr, const int* __restrict__ dst,
                 const int* __restrict__ src, const float4* __restrict__ geom,
                 const float* __restrict__ x, const float* __restrict__ gm,
@@ -513,7 +696,8 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
         const int ne = min(EC, E1 - c0);
         __syncthreads();
         chunk_prologue<H>(D, L, smem, c0, ne, dst, src, geom, W1, W2);
-        chunk_w_gemm_f32<H>(D, L, smem, W3);
+        if constexpr (BF) chunk_w_gemm_bf16<H>(D, L, smem, W3T_h);
+        else chunk_w_gemm_f32<H>(D, L, smem, W3);
         // E: per-edge adjoint of the tensor product
         for (int e = warp; e < ne; e += CONV_WARPS) {
             const int v = s_dst[e], sidx = s_src[e];
@@ -533,19 +717,41 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
             }
         }
         // F: dE/dH2 = dE/dw @ W3^T
-        chunk_gw_gemm_f32<H>(D, L, smem, W3T);
+        if constexpr (BF) chunk_gw_gemm_bf16<H>(D, L, smem, W3_h);
+        else chunk_gw_gemm_f32<H>(D, L, smem, W3T);
         // MLP adjoint: gA2 = gH2 * silu'(A2); gH1 = gA2 @ W2^T; gA1 = gH1 * silu'(A1); gB = gA1 @ W1^T
         float* s_gH = smem + L.gH;
         float* s_A1 = smem + L.A1;
         float* s_A2 = smem + L.A2;
         for (int i = t; i < H * EC; i += CONV_THREADS) s_gH[i] *= dsiluf_(s_A2[i]);
         __syncthreads();
-        for (int i = t; i < H * EC; i += CONV_THREADS) {
-            const int k = i / EC, e = i % EC;
-            float a = 0.0f;
+        {   // gA1 = (gA2 @ W2^T) * silu'(A1), stored over A2; W2T[j][k] = W2[k][j]
+            float ga[(H / 4) * EC / CONV_THREADS > 0 ? (H / 4) * EC / CONV_THREADS : 1][4];
+            int nq = 0;
+            for (int idx = t; idx < (H / 4) * EC; idx += CONV_THREADS, ++nq) {
+                const int kq = idx / EC, e = idx % EC;
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll 8
-            for (int j = 0; j < H; ++j) a = fmaf(s_gH[j * EC + e], __ldg(W2 + k * H + j), a);
-            s_A2[i] = a * dsiluf_(s_A1[i]);          // gA1, stored over A2
+                for (int j = 0; j < H; ++j) {
+                    const float4 b = __ldg(reinterpret_cast<const float4*>(W2T + j * H) + kq);
+                    const float a = s_gH[j * EC + e];
+                    a0 = fmaf(a, b.x, a0);
+                    a1 = fmaf(a, b.y, a1);
+                    a2 = fmaf(a, b.z, a2);
+                    a3 = fmaf(a, b.w, a3);
+                }
+                ga[nq][0] = a0; ga[nq][1] = a1; ga[nq][2] = a2; ga[nq][3] = a3;
+            }
+            __syncthreads();       // every read of A2 (the silu' above) is done
+            nq = 0;
+            for (int idx = t; idx < (H / 4) * EC; idx += CONV_THREADS, ++nq) {
+                const int kq = idx / EC, e = idx % EC;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int o = (4 * kq + q) * EC + e;
+                    s_A2[o] = ga[nq][q] * dsiluf_(s_A1[o]);
+                }
+            }
         }
         __syncthreads();
         float* s_gB = smem + L.stage;              // [NB][EC]
@@ -650,11 +856,15 @@ sevennet_status conv_configure(int H, const std::vector<LayerDev>& layers) {
         return SEVENNET_OK;
     };
     if (H == 64) {
-        SN_TRY(set((const void*)conv_fwd_kernel<64>, need_f));
-        SN_TRY(set((const void*)conv_bwd_kernel<64>, need_b));
+        SN_TRY(set((const void*)conv_fwd_kernel<64, false>, need_f));
+        SN_TRY(set((const void*)conv_bwd_kernel<64, false>, need_b));
+        SN_TRY(set((const void*)conv_fwd_kernel<64, true>, need_f));
+        SN_TRY(set((const void*)conv_bwd_kernel<64, true>, need_b));
     } else if (H == 32) {
-        SN_TRY(set((const void*)conv_fwd_kernel<32>, need_f));
-        SN_TRY(set((const void*)conv_bwd_kernel<32>, need_b));
+        SN_TRY(set((const void*)conv_fwd_kernel<32, false>, need_f));
+        SN_TRY(set((const void*)conv_bwd_kernel<32, false>, need_b));
+        SN_TRY(set((const void*)conv_fwd_kernel<32, true>, need_f));
+        SN_TRY(set((const void*)conv_bwd_kernel<32, true>, need_b));
     } else {
         set_error("radial MLP hidden width must be 32 or 64");
         return SEVENNET_EINVAL;
@@ -667,7 +877,7 @@ size_t conv_smem_need(const ConvDesc& D, int H) { return smem_bytes(D, H, true);
 static int conv_grid(int64_t n_atoms) {
     int dev = 0;
     cudaGetDevice(&dev);
-    int g = num_sms(dev);
+    int g = 2 * num_sms(dev);                 // two CTAs per SM
     if (n_atoms < g) g = (int)(n_atoms > 0 ? n_atoms : 1);
     return g;
 }
@@ -675,32 +885,29 @@ static int conv_grid(int64_t n_atoms) {
 void launch_conv_fwd(const LayerDev& L, int H, sevennet_precision prec, int64_t n_atoms,
                      int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
                      const float4* geom, const float* x, float* m, cudaStream_t st) {
-    (void)prec;
     const int grid = conv_grid(n_atoms);
     const size_t sm = smem_bytes(L.conv, H, false);
-    if (H == 64)
-        conv_fwd_kernel<64><<<grid, CONV_THREADS, sm, st>>>(L.conv, L.mlp0, L.mlp1, L.mlp2, (int)n_atoms,
-                                                            (int)n_edges, row_ptr, dst, src, geom, x, m);
-    else
-        conv_fwd_kernel<32><<<grid, CONV_THREADS, sm, st>>>(L.conv, L.mlp0, L.mlp1, L.mlp2, (int)n_atoms,
-                                                            (int)n_edges, row_ptr, dst, src, geom, x, m);
+    const bool bf = prec == SEVENNET_BF16;
+#define SN_LF(HH, BB) conv_fwd_kernel<HH, BB><<<grid, CONV_THREADS, sm, st>>>(                     \
+        L.conv, L.mlp0, L.mlp1, L.mlp2, L.mlp2h, (int)n_atoms, (int)n_edges, row_ptr, dst, src, geom, x, m)
+    if (H == 64) { if (bf) SN_LF(64, true); else SN_LF(64, false); }
+    else         { if (bf) SN_LF(32, true); else SN_LF(32, false); }
+#undef SN_LF
 }
 
 void launch_conv_bwd(const LayerDev& L, int H, sevennet_precision prec, int64_t n_atoms,
                      int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
                      const float4* geom, const float* x, const float* gm, float* gx,
                      float* gd, cudaStream_t st) {
-    (void)prec;
     const int grid = conv_grid(n_atoms);
     const size_t sm = smem_bytes(L.conv, H, true);
-    if (H == 64)
-        conv_bwd_kernel<64><<<grid, CONV_THREADS, sm, st>>>(L.conv, L.mlp0, L.mlp1, L.mlp2, L.mlp2T,
-                                                            (int)n_atoms, (int)n_edges, row_ptr, dst,
-                                                            src, geom, x, gm, gx, gd);
-    else
-        conv_bwd_kernel<32><<<grid, CONV_THREADS, sm, st>>>(L.conv, L.mlp0, L.mlp1, L.mlp2, L.mlp2T,
-                                                            (int)n_atoms, (int)n_edges, row_ptr, dst,
-                                                            src, geom, x, gm, gx, gd);
+    const bool bf = prec == SEVENNET_BF16;
+#define SN_LB(HH, BB) conv_bwd_kernel<HH, BB><<<grid, CONV_THREADS, sm, st>>>(                     \
+        L.conv, L.mlp0, L.mlp1, L.mlp1T, L.mlp2, L.mlp2T, L.mlp2h, L.mlp2Th, (int)n_atoms,            \
+        (int)n_edges, row_ptr, dst, src, geom, x, gm, gx, gd)
+    if (H == 64) { if (bf) SN_LB(64, true); else SN_LB(64, false); }
+    else         { if (bf) SN_LB(32, true); else SN_LB(32, false); }
+#undef SN_LB
 }
 
 }  // namespace sn

@@ -35,6 +35,14 @@ extern thread_local std::string g_last_error;
         }                                                                          \
     } while (0)
 
+// Entry of a C-ABI call: select the device and drop any error a previous,
+// unrelated runtime call left behind (so it is not reported as ours).
+#define SN_ENTER(dev)                                                              \
+    do {                                                                           \
+        cudaGetLastError();                                                        \
+        SN_CUDA(cudaSetDevice(dev));                                               \
+    } while (0)
+
 #define SN_TRY(expr)                                                               \
     do {                                                                           \
         sevennet_status s_ = (expr);                                               \
@@ -46,7 +54,7 @@ constexpr int MAX_PATHS = 16;
 constexpr int CONV_THREADS = 256;
 constexpr int CONV_WARPS = CONV_THREADS / 32;
 constexpr int MAX_SLOTS = 12;
-constexpr int EC = 32;                 // edges per chunk in the convolution kernels
+constexpr int EC = 16;                 // edges per chunk in the convolution kernels
 constexpr int MAX_NB = 16;             // radial basis functions
 constexpr int MAX_LMAX = 2;
 

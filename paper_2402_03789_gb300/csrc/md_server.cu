@@ -100,7 +100,7 @@ sevennet_status sevennet_md_create(sevennet_model* M, int64_t n_atoms, const int
                                    sevennet_precision prec, sevennet_md** out) {
     SN_CHECK(M && out && species && pos && vel && masses && cell && n_atoms > 0, SEVENNET_EINVAL, "bad argument");
     *out = nullptr;
-    SN_CUDA(cudaSetDevice(M->device));
+    SN_ENTER(M->device);
     for (int s = 0; s < M->cfg.n_species; ++s)
         SN_CHECK(masses[s] > 0 && std::isfinite(masses[s]), SEVENNET_EINVAL, "mass of species %d not positive", s);
     for (int64_t i = 0; i < n_atoms; ++i)
@@ -144,7 +144,7 @@ sevennet_status sevennet_md_create(sevennet_model* M, int64_t n_atoms, const int
 sevennet_status sevennet_md_step(sevennet_md* md, int64_t n_steps, double dt_fs, double* epot_log,
                                  double* ekin_log) {
     SN_CHECK(md && n_steps >= 0 && std::isfinite(dt_fs), SEVENNET_EINVAL, "bad argument");
-    SN_CUDA(cudaSetDevice(md->M->device));
+    SN_ENTER(md->M->device);
     if (n_steps > md->log_cap) {
         cudaFree(md->ekin);
         cudaFree(md->epot);
@@ -176,7 +176,7 @@ sevennet_status sevennet_md_step(sevennet_md* md, int64_t n_steps, double dt_fs,
 
 sevennet_status sevennet_md_get_state(const sevennet_md* md, double* pos, double* vel, double* forces) {
     SN_CHECK(md, SEVENNET_EINVAL, "NULL md");
-    SN_CUDA(cudaSetDevice(md->M->device));
+    SN_ENTER(md->M->device);
     SN_CUDA(cudaStreamSynchronize(md->st));
     const size_t n3 = (size_t)md->N * 3 * sizeof(double);
     if (pos) SN_CUDA(cudaMemcpy(pos, md->pos, n3, cudaMemcpyDeviceToHost));
@@ -205,7 +205,7 @@ struct SrvRes {
     sevennet_status status = SEVENNET_OK;
     double energy = 0, virial[9] = {0};
     std::vector<double> forces;
-    double submit_s = 0, done_s = 0;
+    double submit_s = 0, start_s = 0, done_s = 0;
     int32_t batch_id = -1, batch_structs = 0;
 };
 
@@ -218,6 +218,7 @@ struct SrvSlot {
     std::vector<int64_t> off;
     size_t bytes = 0;
     int32_t batch_id = -1;
+    double start_s = 0;
     int64_t cap_atoms = 0;
     int32_t cap_structs = 0;
     double *pos = nullptr, *forces = nullptr, *energy = nullptr, *virial = nullptr;
@@ -294,6 +295,7 @@ static sevennet_status slot_reserve(SrvSlot& sl, int64_t atoms, int32_t structs)
 // Enqueue one packed batch on a slot (returns after the neighbour count read).
 static sevennet_status slot_launch(sevennet_server* S, SrvSlot& sl) {
     const int32_t ns = (int32_t)sl.reqs.size();
+    sl.start_s = srv_now(S);
     BatchHost b;
     b.n_structs = ns;
     b.atom_off.assign(ns + 1, 0);
@@ -331,6 +333,7 @@ static void slot_finish(sevennet_server* S, SrvSlot& sl, sevennet_status status)
         r.done = true;
         r.status = status;
         r.submit_s = sl.reqs[i].submit_s;
+        r.start_s = sl.start_s;
         r.done_s = now;
         r.batch_id = sl.batch_id;
         r.batch_structs = (int32_t)sl.reqs.size();
@@ -410,7 +413,7 @@ sevennet_status sevennet_server_create(sevennet_model* M, size_t hbm_budget_byte
     SN_CHECK(M && out && n_streams >= 1 && n_streams <= 16 && max_batch_structs >= 1 && hbm_budget_bytes > 0,
              SEVENNET_EINVAL, "bad argument");
     *out = nullptr;
-    SN_CUDA(cudaSetDevice(M->device));
+    SN_ENTER(M->device);
     auto* S = new sevennet_server();
     S->M = M;
     S->budget = hbm_budget_bytes;
@@ -478,6 +481,7 @@ sevennet_status sevennet_server_poll(sevennet_server* S, uint64_t ticket, sevenn
         std::copy(r.virial, r.virial + 9, res->virial);
         if (res->forces) std::copy(r.forces.begin(), r.forces.end(), res->forces);
         res->submit_s = r.submit_s;
+        res->start_s = r.start_s;
         res->done_s = r.done_s;
         res->batch_id = r.batch_id;
         res->batch_structs = r.batch_structs;

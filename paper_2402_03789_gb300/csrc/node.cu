@@ -86,8 +86,94 @@ gemm_f32_kernel(const GemmBatch batch) {
     }
 }
 
+// ---------------------------------------------------------------- BF16 GEMM
+// Tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulate).  64 x 64
+// tile, 8 warps as 4 (rows) x 2 (cols), each warp 16 rows x 32 cols.  A is
+// read as FP32 and rounded to BF16 in the fragment; B is the BF16 [N][K] copy.
+// Activations as hi + lo BF16 pairs (two MMAs), weights as one BF16 value.
+constexpr bool GEMM_SPLIT_ACT = true;
+
+__device__ __forceinline__ void split_bf16_n(float x, float y, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x - hf.x, y - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__device__ __forceinline__ void mma_bf16_n(float* c, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(256)
+gemm_bf16_kernel(const GemmBatch batch) {
+    const GemmProb& P = batch.p[blockIdx.z];
+    const int64_t rows = P.n_atoms * P.R;
+    const int64_t r0 = (int64_t)blockIdx.x * 64;
+    const int n0 = blockIdx.y * 64;
+    if (r0 >= rows || n0 >= P.N) return;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tq = lane & 3;
+    const int wr = warp & 3, wc = warp >> 2;
+    const int nbase = n0 + wc * 32;
+    if (nbase >= P.N) return;
+    const int64_t ra = r0 + wr * 16 + g, rb = ra + 8;
+    auto rowptr = [&](int64_t r) -> const float* {
+        if (r >= rows) return nullptr;
+        const int64_t v = r / P.R;
+        const int mm = (int)(r % P.R);
+        return P.A + v * P.lda + P.a_off + (int64_t)mm * P.K;
+    };
+    const float* pa = rowptr(ra);
+    const float* pb = rowptr(rb);
+    float c[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.0f;
+    const float2 z = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < P.K; k0 += 16) {
+        const int kk = k0 + 2 * tq;
+        const float2 x0 = pa ? *reinterpret_cast<const float2*>(pa + kk) : z;
+        const float2 x1 = pb ? *reinterpret_cast<const float2*>(pb + kk) : z;
+        const float2 x2 = pa ? *reinterpret_cast<const float2*>(pa + kk + 8) : z;
+        const float2 x3 = pb ? *reinterpret_cast<const float2*>(pb + kk + 8) : z;
+        uint32_t a[4], al[4];
+        split_bf16_n(x0.x, x0.y, a[0], al[0]);
+        split_bf16_n(x1.x, x1.y, a[1], al[1]);
+        split_bf16_n(x2.x, x2.y, a[2], al[2]);
+        split_bf16_n(x3.x, x3.y, a[3], al[3]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t* brow = reinterpret_cast<const uint32_t*>(P.Bh + (int64_t)(nbase + j * 8 + g) * P.K);
+            uint32_t b[2] = {__ldg(brow + (kk >> 1)), __ldg(brow + ((kk + 8) >> 1))};
+            mma_bf16_n(c[j], a, b);
+            if (GEMM_SPLIT_ACT) mma_bf16_n(c[j], al, b);
+        }
+    }
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int64_t r = half ? rb : ra;
+        if (r >= rows) continue;
+        const int64_t v = r / P.R;
+        const int mm = (int)(r % P.R);
+        float* cp = P.C + v * P.ldc + P.c_off + (int64_t)mm * P.N;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int col = nbase + j * 8 + 2 * tq;
+            float2 o = make_float2(c[j][2 * half], c[j][2 * half + 1]);
+            if (P.accumulate) {
+                const float2 q = *reinterpret_cast<const float2*>(cp + col);
+                o.x += q.x;
+                o.y += q.y;
+            }
+            *reinterpret_cast<float2*>(cp + col) = o;
+        }
+    }
+}
+
 void launch_gemm(const GemmBatch& b, sevennet_precision prec, cudaStream_t st) {
-    (void)prec;
     if (b.n == 0) return;
     int64_t max_rows = 0;
     int max_n = 0;
@@ -97,7 +183,8 @@ void launch_gemm(const GemmBatch& b, sevennet_precision prec, cudaStream_t st) {
     }
     if (max_rows == 0) return;
     dim3 grid((unsigned)((max_rows + 63) / 64), (unsigned)((max_n + 63) / 64), (unsigned)b.n);
-    gemm_f32_kernel<<<grid, 256, 0, st>>>(b);
+    if (prec == SEVENNET_BF16) gemm_bf16_kernel<<<grid, 256, 0, st>>>(b);
+    else gemm_f32_kernel<<<grid, 256, 0, st>>>(b);
 }
 
 // ---------------------------------------------------------------- embedding

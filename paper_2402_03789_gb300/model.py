@@ -55,9 +55,13 @@ def _prec(p):
     return L.PRECISION[p]
 
 
-def _stream_ptr(stream):
+def _stream_ptr(stream, device=None):
+    """cudaStream_t of `stream`; None means torch's current stream on `device`,
+    so that kernels are ordered with the torch work that made and reads the
+    tensors."""
     if stream is None:
-        return None
+        import torch
+        stream = torch.cuda.current_stream(device)
     return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
 
 
@@ -171,7 +175,7 @@ class SevenNet:
             self.handle, S, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), L.dptr(cells),
             L.iptr(pb) if pb is not None else None, ctypes.c_void_p(species.data_ptr()),
             ctypes.c_void_p(pos.data_ptr()), _prec(precision), ctypes.c_void_p(e.data_ptr()),
-            ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(w.data_ptr()), _stream_ptr(stream)))
+            ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(w.data_ptr()), _stream_ptr(stream, pos.device)))
         return e, f, w
 
     def conv_dims(self, layer):
@@ -189,7 +193,7 @@ class SevenNet:
         L.check(self.lib.sevennet_conv_forward_dev(
             self.handle, layer, n, E, ctypes.c_void_p(row_ptr.data_ptr()), ctypes.c_void_p(src.data_ptr()),
             ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(m.data_ptr()),
-            _prec(precision), _stream_ptr(stream)))
+            _prec(precision), _stream_ptr(stream, x.device)))
         return m
 
     def conv_backward(self, layer, row_ptr, src, d, x, g_m, precision="fp32", stream=None):
@@ -202,7 +206,7 @@ class SevenNet:
             self.handle, layer, n, E, ctypes.c_void_p(row_ptr.data_ptr()), ctypes.c_void_p(src.data_ptr()),
             ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(g_m.data_ptr()),
             ctypes.c_void_p(g_x.data_ptr()), ctypes.c_void_p(g_d.data_ptr()), _prec(precision),
-            _stream_ptr(stream)))
+            _stream_ptr(stream, x.device)))
         return g_x, g_d
 
 
@@ -283,7 +287,7 @@ class Server:
             return None
         del self._n[ticket]
         return dict(energy=res.energy, forces=f, virial=np.array(res.virial[:]).reshape(3, 3),
-                    submit_s=res.submit_s, done_s=res.done_s, batch_id=res.batch_id,
+                    submit_s=res.submit_s, start_s=res.start_s, done_s=res.done_s, batch_id=res.batch_id,
                     batch_structs=res.batch_structs)
 
     def now(self):

@@ -90,3 +90,37 @@ def test_bad_inputs_rejected():
         model.evaluate(np.array([[1.0, 1, 1], [1.0, 1, 1]]), cell, np.array([0, 1]))
     with pytest.raises(sn.SevenNetError):
         model.evaluate(np.array([[0.0, 0, 0]]), np.zeros((3, 3)), np.array([0]))
+
+
+@pytest.mark.parametrize("name,s,spec", CASES[1:], ids=[c[0] for c in CASES[1:]])
+def test_bf16_forces_within_tolerance(name, s, spec):
+    model = get_model(spec)
+    w = normal_weights(oracle.n_params(spec))
+    E, F, W = model.evaluate(s.pos, s.cell, s.species, precision="bf16")
+    Eo, Fo, Wo, *_ = oracle.energy_forces_virial(spec, w, s.species, s.pos, s.cell)
+    e_pa, f_rel, w_rel = errors(E, F, W, Eo, Fo, Wo, s.n_atoms)
+    print(f"bf16 {name}: |dE|/N={e_pa:.2e} F={f_rel:.2e} W={w_rel:.2e}")
+    assert f_rel <= 5e-3
+    assert np.isfinite(E) and np.abs(F.sum(0)).max() <= 1e-9 * np.abs(F).sum()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_batch_equals_alone(prec):
+    import torch
+    spec = MODEL_SEVENNET0
+    model = get_model(spec)
+    structs = [random_structure({"Si": 20, "O": 40}, 2.2, 1.6, seed=31),
+               random_structure({"Si": 6, "N": 8}, 3.1, 1.5, seed=32),
+               random_structure({"Si": 50, "N": 60, "O": 7}, 2.7, 1.5, seed=33)]
+    off = np.cumsum([0] + [s.n_atoms for s in structs])
+    pos = torch.tensor(np.concatenate([s.pos for s in structs]), dtype=torch.float64, device="cuda")
+    sp = torch.tensor(np.concatenate([s.species for s in structs]), dtype=torch.int32, device="cuda")
+    cells = np.stack([s.cell for s in structs])
+    e, f, w = model.evaluate_batch_dev(off, cells, sp, pos, prec)
+    e, f, w = e.cpu().numpy(), f.cpu().numpy(), w.cpu().numpy()
+    # equal up to FP32 summation order (chunk boundaries and adjoint atomics move
+    # with the batch), i.e. within the FP32 path's stated tolerances
+    for i, s in enumerate(structs):
+        E1, F1, W1 = model.evaluate(s.pos, s.cell, s.species, prec)
+        e_pa, f_rel, w_rel = errors(e[i], f[off[i]:off[i + 1]], w[i], E1, F1, W1, s.n_atoms)
+        assert e_pa <= 1e-6 and f_rel <= 1e-5 and w_rel <= 1e-5, (i, e_pa, f_rel, w_rel)
