@@ -22,6 +22,16 @@ Model definition (readings of the points the paper leaves open):
   E_v = scale * R2(R1(h^(T+1)_0e)) + shift[Z_v]              (Eq. 1: E = sum_v E_v)
   Linears act per irrep l on the channel index, out = in @ W / sqrt(mul_in).
 
+Pins (tests/test_oracle_*.py): parameter count 842,432 = "0.84 million"
+(Sec. 5.1); rotation / translation / permutation invariance; extensivity;
+zero net force; forces and virial against central finite differences;
+closed-form messages of one edge for the identity / dot / cross couplings.
+Parity unpinned: the normalisation constants (1/sqrt(fan_in) of the MLP and
+linears, 1/avg_num_neigh, the readout widths), the SiLU activations of the gate
+and the envelope order p are readings of points the paper leaves open; no
+reference values of the real SevenNet exist to pin them, so they are fixed only
+by agreement between this oracle and the CUDA library.
+
 Canonical weight order (one flat FP64 vector): embed [n_species, mul0]; then per
 block: sc[l] [mul_in, mul_y] for l in Y and In (ascending l), lin1[l] [mul, mul]
 for l in In, mlp0 [n_basis, H], mlp1 [H, H], mlp2 [H, W] (columns: path-major,
