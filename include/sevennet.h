@@ -196,6 +196,25 @@ sevennet_status sevennet_conv_backward_dev(sevennet_model* model, int32_t layer,
                                            const float* d, const float* x, const float* g_m,
                                            float* g_x, float* g_d, sevennet_precision prec,
                                            void* stream);
+/* The forward of sevennet_conv_forward_dev for callers that may not allocate
+ * device memory during the call (a fixed memory plan, or code that must not
+ * risk the synchronisation an allocation or free can bring).  No counterpart
+ * in the paper.  Arguments, layouts and results are those of
+ * sevennet_conv_forward_dev; the per-edge scratch lives in one static device
+ * array of the library (5 MiB, held by every GPU that loads the library until
+ * exit) instead of being allocated.  Limits and behaviour:
+ *   - n_edges <= 262144, else EINVAL and nothing is launched;
+ *   - no cudaMalloc / cudaFree / allocating library call is made;
+ *   - the first call on a device looks up the array's address (set-up), so
+ *     make that first call before any stream capture;
+ *   - every call reuses the same array: calls whose kernels overlap on the GPU
+ *     race; order them on one stream or with events.
+ * row_ptr must be a valid CSR (row_ptr[0] = 0, row_ptr[n_atoms] = n_edges). */
+sevennet_status sevennet_conv_forward_noalloc(sevennet_model* model, int32_t layer,
+                                              int64_t n_atoms, int64_t n_edges,
+                                              const int32_t* row_ptr, const int32_t* src,
+                                              const float* d, const float* x, float* m_out,
+                                              sevennet_precision prec, void* stream);
 /* Row widths used by the conv entry points: x_dim and m_dim of block layer. */
 sevennet_status sevennet_conv_dims(const sevennet_model* model, int32_t layer,
                                    int32_t* x_dim, int32_t* m_dim);

@@ -83,6 +83,7 @@ SIGNATURES = {
     "sevennet_conv_forward_dev": (_I32, [_P, _I32, _I64, _I64, _P, _P, _P, _P, _P, ctypes.c_int, _P]),
     "sevennet_conv_backward_dev": (_I32, [_P, _I32, _I64, _I64, _P, _P, _P, _P, _P, _P, _P,
                                           ctypes.c_int, _P]),
+    "sevennet_conv_forward_noalloc": (_I32, [_P, _I32, _I64, _I64, _P, _P, _P, _P, _P, ctypes.c_int, _P]),
     "sevennet_conv_dims": (_I32, [_P, _I32, _IP, _IP]),
     "sevennet_md_create": (_I32, [_P, _I64, _IP, _D, _D, _D, _D, ctypes.c_int, ctypes.POINTER(_P)]),
     "sevennet_md_step": (_I32, [_P, _I64, ctypes.c_double, _D, _D]),
