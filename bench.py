@@ -51,19 +51,25 @@ def block_paths(spec, t):
     return out
 
 
-def conv_flops_per_edge(spec, t, adjoint):
-    """Algorithmic FLOPs of the fused convolution kernel per edge for block t."""
+def conv_flops_per_edge(spec, t, adjoint, tensor_core):
+    """Algorithmic FLOPs of the fused convolution kernel per edge for block t,
+    split into (FFMA work, tensor-core work).  With tensor_core, the MLP matrix
+    products with H-wide inputs (H x H and H x W) run on tensor cores."""
     H, NB = spec.mlp_hidden, spec.n_basis
     paths = block_paths(spec, t)
     W = sum(p[3] for p in paths)
-    mlp = 2 * (NB * H + H * H + H * W)
+    first = 2 * NB * H                                         # basis -> hidden, FFMA always
+    mm = 2 * (H * H + H * W)                                   # hidden -> hidden -> W
     g = sum(2 * CG_NNZ[p[:3]] for p in paths)                 # G matrices
     if not adjoint:
         tp = sum(2 * mu * ((2 * l1 + 1) * (2 * l3 + 1) + (2 * l3 + 1)) for l1, l2, l3, mu in paths)
-        return mlp + g + tp
+        mlp_alu, mlp_tc = (first, mm) if tensor_core else (first + mm, 0)
+        return mlp_alu + g + tp, mlp_tc
     tp = sum(2 * mu * ((2 * l1 + 1) * (2 * l3 + 1) + 2 * (2 * l1 + 1) + CG_NNZ[(l1, l2, l3)])
              for l1, l2, l3, mu in paths)
-    return 2 * mlp + g + tp            # forward recompute + input gradient of the MLP
+    # forward recompute + input gradient of the MLP
+    mlp_alu, mlp_tc = (2 * first, 2 * mm) if tensor_core else (2 * (first + mm), 0)
+    return mlp_alu + g + tp, mlp_tc
 
 
 def fp32_alu_peak_tflops(n_sm, clock_mhz):
@@ -182,6 +188,53 @@ def traffic_for(kernel, source):
     return None
 
 
+def serving_run(sn, model, precision, n_requests=512, rate_hz=200.0, budget_gb=8.0, n_streams=4,
+                max_batch=32):
+    """Replay the Poisson request stream through the continuous-batching server.
+
+    Requests are submitted at their arrival times; latency = completion - arrival
+    on the server clock.  Returns p50/p99 latency, throughput and batching stats.
+    """
+    from synth import serving_trace
+    trace = serving_trace(n_requests, rate_hz, seed=6)
+    srv = sn.Server(model, hbm_budget_bytes=int(budget_gb * (1 << 30)), n_streams=n_streams,
+                    max_batch_structs=max_batch, precision=precision)
+    # warm the server's buffers with a few requests (not counted)
+    warm = [srv.submit(st.pos, st.cell, st.species) for _, st in trace[:8]]
+    for t in warm:
+        while srv.poll(t) is None:
+            time.sleep(0.0005)
+    t0 = srv.now()
+    pending, done = {}, {}
+    i = 0
+    while i < len(trace) or pending:
+        now = srv.now() - t0
+        while i < len(trace) and trace[i][0] <= now:
+            st = trace[i][1]
+            pending[srv.submit(st.pos, st.cell, st.species)] = (i, st.n_atoms)
+            i += 1
+        for tk in list(pending):
+            r = srv.poll(tk)
+            if r is not None:
+                done[tk] = (r, pending.pop(tk)[1])
+        if i < len(trace):
+            time.sleep(max(0.0, min(0.0005, trace[i][0] - (srv.now() - t0))))
+        else:
+            time.sleep(0.0002)
+    srv.close()
+    lat = sorted((r["done_s"] - r["submit_s"]) * 1e3 for r, _ in done.values())
+    first = min(r["submit_s"] for r, _ in done.values())
+    last = max(r["done_s"] for r, _ in done.values())
+    atoms = sum(n for _, n in done.values())
+    bsz = [r["batch_structs"] for r, _ in done.values()]
+    return {"requests": len(done), "rate_hz": rate_hz, "p50_ms": lat[len(lat) // 2],
+            "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "max_ms": lat[-1],
+            "atom_steps_per_s": atoms / (last - first), "mean_batch_structs": sum(bsz) / len(bsz),
+            "streams": n_streams, "hbm_budget_gb": budget_gb, "precision": precision,
+            "trace": f"{n_requests} cells of 16-2000 atoms (log-uniform), Si/N/O, 2.2-3.1 g/cm3, "
+                     f"Poisson arrivals at {rate_hz:.0f}/s"}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -208,6 +261,7 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--no-compare", action="store_true", help="skip the other precision's line")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream measurement")
     ap.add_argument("--workload", default=WORKLOAD)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -283,14 +337,24 @@ def main():
     # roofline of the dominant kernel family (the convolution adjoint)
     fam = max(("conv_bwd", "conv_fwd"), key=lambda k: prof.get(k, (0, 0))[0])
     tot_ms, n_launch = prof[fam]
-    flops_step = sum(conv_flops_per_edge(spec, t, fam == "conv_bwd") * n_edges for t in range(spec.n_layers))
-    achieved = flops_step * args.steps / (tot_ms / 1e3) / 1e12
+    tc = args.precision == "bf16"
+    per = [conv_flops_per_edge(spec, t, fam == "conv_bwd", tc) for t in range(spec.n_layers)]
+    alu_step = sum(a for a, _ in per) * n_edges
+    tc_step = sum(b for _, b in per) * n_edges
+    achieved = alu_step * args.steps / (tot_ms / 1e3) / 1e12
     peak = fp32_alu_peak_tflops(n_sm, 2070.0)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic_for(fam, os.path.join(ROOT, "paper_2402_03789_gb300", "csrc", "conv.cu")),
                 "kernel": fam, "share_of_step": tot_ms / dev_ms,
                 "peak_source": f"FP32 FFMA: {n_sm} SMs x 128 lanes x 2 FLOP x 2070 MHz (unit counts and max clock)",
-                "flops_per_step": flops_step}
+                "alu_flops_per_step": alu_step}
+    if tc:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
+        t_ach = tc_step * args.steps / (tot_ms / 1e3) / 1e12
+        roofline["tensor"] = {"achieved": t_ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                              "frac": t_ach / peaks["bf16_tflops"], "flops_per_step": tc_step,
+                              "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -311,6 +375,9 @@ def main():
         o_ms, *_ = timed(other)
         line["compare"] = {other: {"value": world * s.n_atoms * args.steps / (o_ms / 1e3),
                                    "ms_per_step": o_ms / args.steps}}
+
+    if not args.no_serving and rank == 0:
+        line["serving"] = serving_run(sn, model, args.precision)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         base, (s2, spec2, w2, res) = oracle_sample()

@@ -188,14 +188,26 @@ static std::vector<__nv_bfloat16> to_bf16(const std::vector<float>& f) {
     return o;
 }
 
+// hi = bf16(w) followed by lo = bf16(w - hi): two BF16 terms that carry w to
+// about 16 mantissa bits (used where a tensor-core product takes both).
+static std::vector<__nv_bfloat16> to_bf16_pair(const std::vector<float>& f) {
+    std::vector<__nv_bfloat16> o(2 * f.size());
+    for (size_t i = 0; i < f.size(); ++i) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(f[i]);
+        o[i] = h;
+        o[f.size() + i] = __float2bfloat16_rn(f[i] - __bfloat162float(h));
+    }
+    return o;
+}
+
 static sevennet_status upload_linear(sevennet_model* M, const double* w, int rows, int cols, double s,
                                      float** W, float** WT, __nv_bfloat16** Wh, __nv_bfloat16** WTh) {
     auto a = scaled(w, rows, cols, s, false);
     auto b = scaled(w, rows, cols, s, true);
     SN_TRY(dev_upload(M, a, W));
     SN_TRY(dev_upload(M, b, WT));
-    SN_TRY(dev_upload(M, to_bf16(b), Wh));     // [cols][rows]: N-major B operand of out = in @ W
-    SN_TRY(dev_upload(M, to_bf16(a), WTh));    // [rows][cols]: N-major B operand of gin = gout @ W^T
+    SN_TRY(dev_upload(M, to_bf16_pair(b), Wh));   // [cols][rows] hi, then lo: B operand of out = in @ W
+    SN_TRY(dev_upload(M, to_bf16_pair(a), WTh));  // [rows][cols] hi, then lo: B operand of gin = gout @ W^T
     return SEVENNET_OK;
 }
 
@@ -536,7 +548,7 @@ sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const do
             P.g_off = goff;
             col += q.mul;
             ch[q.l3] += q.mul;
-            goff += (2 * q.l1 + 1) * (2 * q.l3 + 1);
+            goff += ((2 * q.l1 + 1) * (2 * q.l3 + 1) + 3) & ~3;   // 16-byte aligned G blocks
         }
         for (int l = 0; l < 3; ++l) {
             int b = -1, e = -1;
@@ -599,6 +611,8 @@ sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const do
             if ((s = dev_upload(M, w1, &L.mlp1))) return fail(s);
             auto w1T = scaled(weights + e1->off, H, H, 1.0 / std::sqrt((double)H), true);
             if ((s = dev_upload(M, w1T, &L.mlp1T))) return fail(s);
+            if ((s = dev_upload(M, to_bf16_pair(w1), &L.mlp1h))) return fail(s);     // [k][j] hi, lo
+            if ((s = dev_upload(M, to_bf16_pair(w1T), &L.mlp1Th))) return fail(s);   // [j][k] hi, lo
             if ((s = dev_upload(M, w2, &L.mlp2))) return fail(s);
             if ((s = dev_upload(M, w2T, &L.mlp2T))) return fail(s);
             if ((s = dev_upload(M, to_bf16(w2T), &L.mlp2h))) return fail(s);   // [W][H]

@@ -122,136 +122,6 @@ __device__ __forceinline__ void path_G(int kind, const float* Y, float* g) {
     }
 }
 
-// Phases A-C shared by both kernels.  Leaves s_src/s_dst/Y/B/A1/A2/H2/G filled.
-template <int H>
-__device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem& L, float* smem,
-                                               int c0, int ne, const int* __restrict__ dst,
-                                               const int* __restrict__ src,
-                                               const float4* __restrict__ geom,
-                                               const float* __restrict__ W1,
-                                               const float* __restrict__ W2) {
-    const int t = threadIdx.x;
-    int* s_src = reinterpret_cast<int*>(smem + L.src);
-    int* s_dst = reinterpret_cast<int*>(smem + L.dst);
-    float* s_Y = smem + L.Y;
-    float* s_B = smem + L.B;       // [NB][EC]
-    if (t < EC) {
-        if (t < ne) {
-            const int ge = c0 + t;
-            s_src[t] = src[ge];
-            s_dst[t] = dst[ge];
-            edge_features(D, geom[ge], s_Y + t * 9, s_B + t, EC);
-        } else {
-            s_src[t] = 0;
-            s_dst[t] = -1;
-            for (int i = 0; i < 9; ++i) s_Y[t * 9 + i] = 0.0f;
-            for (int n = 0; n < D.n_basis; ++n) s_B[n * EC + t] = 0.0f;
-        }
-    }
-    __syncthreads();
-    // B: A1 = B @ W1 (layout [H][EC]); H1 = silu(A1) lives in the staging area until phase D
-    float* s_A1 = smem + L.A1;
-    float* s_A2 = smem + L.A2;
-    float* s_H2 = smem + L.H2;
-    float* s_H1 = smem + L.stage;
-    for (int i = t; i < H * EC; i += CONV_THREADS) {
-        const int j = i / EC, e = i % EC;
-        float a = 0.0f;
-        for (int n = 0; n < D.n_basis; ++n) a = fmaf(s_B[n * EC + e], __ldg(W1 + n * H + j), a);
-        s_A1[i] = a;
-        s_H1[i] = siluf_(a);
-    }
-    // C: G matrices (independent of B)
-    float* s_G = smem + L.G;
-    for (int i = t; i < EC * D.n_paths; i += CONV_THREADS) {
-        const int e = i % EC, p = i / EC;
-        path_G(D.paths[p].kind, s_Y + e * 9, s_G + e * D.nG + D.paths[p].g_off);
-    }
-    __syncthreads();
-    // A2 = H1 @ W2, H2 = silu(A2): each thread computes 4 hidden units of one edge
-    for (int idx = t; idx < (H / 4) * EC; idx += CONV_THREADS) {
-        const int jq = idx / EC, e = idx % EC;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll 8
-        for (int k = 0; k < H; ++k) {
-            const float4 b = __ldg(reinterpret_cast<const float4*>(W2 + k * H) + jq);
-            const float a = s_H1[k * EC + e];
-            a0 = fmaf(a, b.x, a0);
-            a1 = fmaf(a, b.y, a1);
-            a2 = fmaf(a, b.z, a2);
-            a3 = fmaf(a, b.w, a3);
-        }
-        const float av[4] = {a0, a1, a2, a3};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int o = (4 * jq + q) * EC + e;
-            s_A2[o] = av[q];
-            s_H2[o] = siluf_(av[q]);
-        }
-    }
-    __syncthreads();
-}
-
-// Phase D (FP32): w[e][c] = sum_k H2[k][e] W3[k][c] for all W columns.
-template <int H>
-__device__ __forceinline__ void chunk_w_gemm_f32(const ConvDesc& D, const ConvSmem& L, float* smem,
-                                                 const float* __restrict__ W3) {
-    constexpr int NEG = EC / 4;                 // groups of 4 edges
-    constexpr int NCG = CONV_THREADS / NEG;     // column-quad threads per edge group
-    constexpr int NQ = DCOLS / (4 * NCG);       // column quads per thread and pass
-    const int t = threadIdx.x;
-    const int eg = t / NCG, cg = t % NCG;
-    const float* s_H2 = smem + L.H2;
-    float4* st4 = reinterpret_cast<float4*>(smem + L.stage);   // [KS][DCOLS/4]
-    float* s_w = smem + L.w;
-    const int W = D.W;
-    for (int cb = 0; cb < W; cb += DCOLS) {
-        float acc[4][NQ][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < NQ; ++j)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
-        for (int k0 = 0; k0 < H; k0 += KS) {
-            __syncthreads();
-            for (int i = t; i < KS * (DCOLS / 4); i += CONV_THREADS) {
-                const int kk = i / (DCOLS / 4), q = i % (DCOLS / 4);
-                const int col = cb + 4 * q;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (col < W) v = __ldg(reinterpret_cast<const float4*>(W3 + (size_t)(k0 + kk) * W + col));
-                st4[i] = v;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int kk = 0; kk < KS; ++kk) {
-                const float4 a = *reinterpret_cast<const float4*>(s_H2 + (k0 + kk) * EC + 4 * eg);
-                const float av[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-                for (int j = 0; j < NQ; ++j) {
-                    const float4 b = st4[kk * (DCOLS / 4) + cg + NCG * j];
-                    const float bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[i][j][q] = fmaf(av[i], bv[q], acc[i][j][q]);
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < NQ; ++j) {
-            const int col = cb + 4 * (cg + NCG * j);
-            if (col < W) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    *reinterpret_cast<float4*>(s_w + (4 * eg + i) * D.Wpad + col) =
-                        make_float4(acc[i][j][0], acc[i][j][1], acc[i][j][2], acc[i][j][3]);
-            }
-        }
-    }
-    __syncthreads();
-}
-
 // ---- BF16 tensor-core variants of phases D and F (mma.sync m16n8k16, FP32 accumulate)
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -336,67 +206,221 @@ __device__ __forceinline__ void chunk_w_gemm_bf16(const ConvDesc& D, const ConvS
 }
 
 // Phase F (BF16): gH2[k][e] = sum_c gw[e][c] W3[k][c]; B operand W3 [H][W] (bf16).
+// The K (column) range is split over the warps, so each dE/dw fragment is read
+// and split once; partial sums meet in shared memory.
 template <int H>
 __device__ __forceinline__ void chunk_gw_gemm_bf16(const ConvDesc& D, const ConvSmem& L, float* smem,
                                                    const __nv_bfloat16* __restrict__ W3h) {
     constexpr int NT = H / 8;                  // n tiles of 8 hidden units
-    constexpr int KSPLIT = CONV_WARPS / NT;    // warps sharing one n tile split K
-    constexpr int MT = EC / 16;
+    static_assert(EC == 16, "one m tile of edges");
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tq = lane & 3;
-    const int nt = warp % NT, kp = warp / NT;
     const float* s_w = smem + L.w;
+    float* s_gH = smem + L.gH;                 // [H][EC]
     const int W = D.W;
+    for (int i = t; i < H * EC; i += CONV_THREADS) s_gH[i] = 0.0f;
     __syncthreads();
-    float c[MT][4];
+    float c[NT][4];
 #pragma unroll
-    for (int mt = 0; mt < MT; ++mt) c[mt][0] = c[mt][1] = c[mt][2] = c[mt][3] = 0.f;
-    const uint32_t* brow = reinterpret_cast<const uint32_t*>(W3h + (size_t)(nt * 8 + g) * W);
-    for (int ks = kp; ks < W / 16; ks += KSPLIT) {
+    for (int nt = 0; nt < NT; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
+    for (int ks = warp; ks < W / 16; ks += CONV_WARPS) {
         const int c0 = ks * 16 + 2 * tq;
-        uint32_t b[2] = {__ldg(brow + (c0 >> 1)), __ldg(brow + ((c0 + 8) >> 1))};
+        const float2 x0 = *reinterpret_cast<const float2*>(s_w + g * D.Wpad + c0);
+        const float2 x1 = *reinterpret_cast<const float2*>(s_w + (g + 8) * D.Wpad + c0);
+        const float2 x2 = *reinterpret_cast<const float2*>(s_w + g * D.Wpad + c0 + 8);
+        const float2 x3 = *reinterpret_cast<const float2*>(s_w + (g + 8) * D.Wpad + c0 + 8);
+        uint32_t a[4], al[4];
+        split_bf16(x0.x, x0.y, a[0], al[0]);
+        split_bf16(x1.x, x1.y, a[1], al[1]);
+        split_bf16(x2.x, x2.y, a[2], al[2]);
+        split_bf16(x3.x, x3.y, a[3], al[3]);
 #pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-            const int e = mt * 16 + g;
-            const float2 x0 = *reinterpret_cast<const float2*>(s_w + e * D.Wpad + c0);
-            const float2 x1 = *reinterpret_cast<const float2*>(s_w + (e + 8) * D.Wpad + c0);
-            const float2 x2 = *reinterpret_cast<const float2*>(s_w + e * D.Wpad + c0 + 8);
-            const float2 x3 = *reinterpret_cast<const float2*>(s_w + (e + 8) * D.Wpad + c0 + 8);
-            uint32_t a[4], al[4];
-            split_bf16(x0.x, x0.y, a[0], al[0]);
-            split_bf16(x1.x, x1.y, a[1], al[1]);
-            split_bf16(x2.x, x2.y, a[2], al[2]);
-            split_bf16(x3.x, x3.y, a[3], al[3]);
-            mma_bf16(c[mt], a, b);
-            if constexpr (SPLIT_ACT) mma_bf16(c[mt], al, b);
+        for (int nt = 0; nt < NT; ++nt) {
+            const uint32_t* brow = reinterpret_cast<const uint32_t*>(W3h + (size_t)(nt * 8 + g) * W);
+            const uint32_t b[2] = {__ldg(brow + (c0 >> 1)), __ldg(brow + ((c0 + 8) >> 1))};
+            mma_bf16(c[nt], a, b);
+            if constexpr (SPLIT_ACT) mma_bf16(c[nt], al, b);
         }
     }
-    float* s_gH = smem + L.gH;                 // [H][EC]
-    float* red = smem + L.stage;               // [KSPLIT-1][8 warps' tiles]
-    const int k = nt * 8 + 2 * tq;
-    if (KSPLIT > 1) {
-        if (kp > 0) {
 #pragma unroll
-            for (int mt = 0; mt < MT; ++mt)
+    for (int nt = 0; nt < NT; ++nt) {
+        const int k = nt * 8 + 2 * tq;
+        atomicAdd(s_gH + k * EC + g, c[nt][0]);
+        atomicAdd(s_gH + (k + 1) * EC + g, c[nt][1]);
+        atomicAdd(s_gH + k * EC + g + 8, c[nt][2]);
+        atomicAdd(s_gH + (k + 1) * EC + g + 8, c[nt][3]);
+    }
+    __syncthreads();
+}
+
+// Hidden layer of the radial MLP on tensor cores (BF16 path):
+//   out[k_out][e] = sum_k in[k][e] B[k][k_out], B given N-major ([k_out][k]) as a
+//   hi + lo BF16 pair; three MMAs per k step (hi*hi, lo*hi, hi*lo).
+// The 16 edges of the chunk are one m tile; warps take n tiles of 8 outputs.
+template <int H>
+__device__ __forceinline__ void hidden_mma(const float* __restrict__ s_in, const __nv_bfloat16* __restrict__ Bn,
+                                           float (&c)[4], int nt) {
+    constexpr int KSN = H / 16;
+    const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+    c[0] = c[1] = c[2] = c[3] = 0.f;
+    const uint32_t* brow = reinterpret_cast<const uint32_t*>(Bn + (size_t)(nt * 8 + g) * H);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) red[((kp - 1) * NT + nt) * 256 + (mt * 4 + q) * 32 + lane] = c[mt][q];
+    for (int ks = 0; ks < KSN; ++ks) {
+        const int k0 = ks * 16 + 2 * tq;
+        uint32_t a[4], al[4];
+        split_bf16(s_in[k0 * EC + g], s_in[(k0 + 1) * EC + g], a[0], al[0]);
+        split_bf16(s_in[k0 * EC + g + 8], s_in[(k0 + 1) * EC + g + 8], a[1], al[1]);
+        split_bf16(s_in[(k0 + 8) * EC + g], s_in[(k0 + 9) * EC + g], a[2], al[2]);
+        split_bf16(s_in[(k0 + 8) * EC + g + 8], s_in[(k0 + 9) * EC + g + 8], a[3], al[3]);
+        const uint32_t b[2] = {__ldg(brow + (k0 >> 1)), __ldg(brow + ((k0 + 8) >> 1))};
+        const uint32_t bl[2] = {__ldg(brow + H * H / 2 + (k0 >> 1)), __ldg(brow + H * H / 2 + ((k0 + 8) >> 1))};
+        mma_bf16(c, a, b);
+        if constexpr (SPLIT_ACT) mma_bf16(c, al, b);
+        mma_bf16(c, a, bl);
+    }
+}
+
+// Phases A-C shared by both kernels.  Leaves s_src/s_dst/Y/B/A1/A2/H2/G filled.
+template <int H, bool BF>
+__device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem& L, float* smem,
+                                               int c0, int ne, const int* __restrict__ dst,
+                                               const int* __restrict__ src,
+                                               const float4* __restrict__ geom,
+                                               const float* __restrict__ W1,
+                                               const float* __restrict__ W2,
+                                               const __nv_bfloat16* __restrict__ W2T_h) {
+    const int t = threadIdx.x;
+    int* s_src = reinterpret_cast<int*>(smem + L.src);
+    int* s_dst = reinterpret_cast<int*>(smem + L.dst);
+    float* s_Y = smem + L.Y;
+    float* s_B = smem + L.B;       // [NB][EC]
+    if (t < EC) {
+        if (t < ne) {
+            const int ge = c0 + t;
+            s_src[t] = src[ge];
+            s_dst[t] = dst[ge];
+            edge_features(D, geom[ge], s_Y + t * 9, s_B + t, EC);
+        } else {
+            s_src[t] = 0;
+            s_dst[t] = -1;
+            for (int i = 0; i < 9; ++i) s_Y[t * 9 + i] = 0.0f;
+            for (int n = 0; n < D.n_basis; ++n) s_B[n * EC + t] = 0.0f;
+        }
+    }
+    __syncthreads();
+    // B: A1 = B @ W1 (layout [H][EC]); H1 = silu(A1) lives in the staging area until phase D
+    float* s_A1 = smem + L.A1;
+    float* s_A2 = smem + L.A2;
+    float* s_H2 = smem + L.H2;
+    float* s_H1 = smem + L.stage;
+    for (int i = t; i < H * EC; i += CONV_THREADS) {
+        const int j = i / EC, e = i % EC;
+        float a = 0.0f;
+        for (int n = 0; n < D.n_basis; ++n) a = fmaf(s_B[n * EC + e], __ldg(W1 + n * H + j), a);
+        s_A1[i] = a;
+        s_H1[i] = siluf_(a);
+    }
+    // C: G matrices (independent of B)
+    float* s_G = smem + L.G;
+    for (int i = t; i < EC * D.n_paths; i += CONV_THREADS) {
+        const int e = i % EC, p = i / EC;
+        path_G(D.paths[p].kind, s_Y + e * 9, s_G + e * D.nG + D.paths[p].g_off);
+    }
+    __syncthreads();
+    if constexpr (BF) {          // A2 = H1 @ W2 on tensor cores, H2 = silu(A2)
+        const int warp = t >> 5, lane = t & 31, g = lane >> 2, tq = lane & 3;
+        for (int nt = warp; nt < H / 8; nt += CONV_WARPS) {
+            float c[4];
+            hidden_mma<H>(s_H1, W2T_h, c, nt);
+            const int j = nt * 8 + 2 * tq;
+            const int o[4] = {j * EC + g, (j + 1) * EC + g, j * EC + g + 8, (j + 1) * EC + g + 8};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                s_A2[o[q]] = c[q];
+                s_H2[o[q]] = siluf_(c[q]);
+            }
         }
         __syncthreads();
-        if (kp == 0) {
-            for (int j = 1; j < KSPLIT; ++j)
+        return;
+    }
+    // A2 = H1 @ W2, H2 = silu(A2): each thread computes 4 hidden units of one edge
+    for (int idx = t; idx < (H / 4) * EC; idx += CONV_THREADS) {
+        const int jq = idx / EC, e = idx % EC;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < H; ++k) {
+            const float4 b = __ldg(reinterpret_cast<const float4*>(W2 + k * H) + jq);
+            const float a = s_H1[k * EC + e];
+            a0 = fmaf(a, b.x, a0);
+            a1 = fmaf(a, b.y, a1);
+            a2 = fmaf(a, b.z, a2);
+            a3 = fmaf(a, b.w, a3);
+        }
+        const float av[4] = {a0, a1, a2, a3};
 #pragma unroll
-                for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) c[mt][q] += red[((j - 1) * NT + nt) * 256 + (mt * 4 + q) * 32 + lane];
+        for (int q = 0; q < 4; ++q) {
+            const int o = (4 * jq + q) * EC + e;
+            s_A2[o] = av[q];
+            s_H2[o] = siluf_(av[q]);
         }
     }
-    if (kp == 0) {
+    __syncthreads();
+}
+
+// Phase D (FP32): w[e][c] = sum_k H2[k][e] W3[k][c] for all W columns.
+template <int H>
+__device__ __forceinline__ void chunk_w_gemm_f32(const ConvDesc& D, const ConvSmem& L, float* smem,
+                                                 const float* __restrict__ W3) {
+    constexpr int NEG = EC / 4;                 // groups of 4 edges
+    constexpr int NCG = CONV_THREADS / NEG;     // column-quad threads per edge group
+    constexpr int NQ = DCOLS / (4 * NCG);       // column quads per thread and pass
+    const int t = threadIdx.x;
+    const int eg = t / NCG, cg = t % NCG;
+    const float* s_H2 = smem + L.H2;
+    float4* st4 = reinterpret_cast<float4*>(smem + L.stage);   // [KS][DCOLS/4]
+    float* s_w = smem + L.w;
+    const int W = D.W;
+    for (int cb = 0; cb < W; cb += DCOLS) {
+        float acc[4][NQ][4];
 #pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-            const int e = mt * 16 + g;
-            s_gH[k * EC + e] = c[mt][0];
-            s_gH[(k + 1) * EC + e] = c[mt][1];
-            s_gH[k * EC + e + 8] = c[mt][2];
-            s_gH[(k + 1) * EC + e + 8] = c[mt][3];
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < NQ; ++j)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
+        for (int k0 = 0; k0 < H; k0 += KS) {
+            __syncthreads();
+            for (int i = t; i < KS * (DCOLS / 4); i += CONV_THREADS) {
+                const int kk = i / (DCOLS / 4), q = i % (DCOLS / 4);
+                const int col = cb + 4 * q;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (col < W) v = __ldg(reinterpret_cast<const float4*>(W3 + (size_t)(k0 + kk) * W + col));
+                st4[i] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < KS; ++kk) {
+                const float4 a = *reinterpret_cast<const float4*>(s_H2 + (k0 + kk) * EC + 4 * eg);
+                const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+                for (int j = 0; j < NQ; ++j) {
+                    const float4 b = st4[kk * (DCOLS / 4) + cg + NCG * j];
+                    const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[i][j][q] = fmaf(av[i], bv[q], acc[i][j][q]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) {
+            const int col = cb + 4 * (cg + NCG * j);
+            if (col < W) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    *reinterpret_cast<float4*>(s_w + (4 * eg + i) * D.Wpad + col) =
+                        make_float4(acc[i][j][0], acc[i][j][1], acc[i][j][2], acc[i][j][3]);
+            }
         }
     }
     __syncthreads();
@@ -426,6 +450,21 @@ __device__ __forceinline__ void cta_range(int n_atoms, int n_edges, const int* _
 }
 
 // ------------------------------------------------------------- forward
+// G matrix of one path into registers with 16-byte shared-memory loads
+// (every path's G starts on a 16-byte boundary).
+template <int NG>
+__device__ __forceinline__ void load_G(const float* __restrict__ src, float* G) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int i = 0; i < (NG + 3) / 4; ++i) {
+        const float4 v = s4[i];
+        G[4 * i] = v.x;
+        G[4 * i + 1] = v.y;
+        G[4 * i + 2] = v.z;
+        G[4 * i + 3] = v.w;
+    }
+}
+
 template <int L1, int L2, int L3>
 __device__ __forceinline__ void tp_fwd_group(const PathDesc& P, int u, int c0, int ne,
                                              const float* s_w, int Wpad, const float* s_G, int nG,
@@ -473,7 +512,8 @@ __device__ __forceinline__ void tp_fwd_group(const PathDesc& P, int u, int c0, i
                 for (int c = 0; c < N3; ++c) acc[c] = 0.0f;
             }
             const float wv = s_w[e * Wpad + col];
-            const float* G = s_G + e * nG + P.g_off;
+            float G[((N1 * N3 + 3) / 4) * 4];
+            load_G<N1 * N3>(s_G + e * nG + P.g_off, G);
 #pragma unroll
             for (int c = 0; c < N3; ++c) {
                 float tt = 0.0f;
@@ -490,7 +530,7 @@ template <int H, bool BF>
 __global__ void __launch_bounds__(CONV_THREADS, 2)
 conv_fwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __restrict__ W2,
                 const float* __restrict__ W3, const __nv_bfloat16* __restrict__ W3T_h,
-                int n_atoms, int n_edges,
+                const __nv_bfloat16* __restrict__ W2T_h, int n_atoms, int n_edges,
                 const int* __restrict__ row_ptr, const int* __restrict__ dst,
                 const int* __restrict__ src, const float4* __restrict__ geom,
                 const float* __restrict__ x, float* __restrict__ m) {
@@ -513,7 +553,7 @@ conv_fwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
     for (int c0 = E0; c0 < E1; c0 += EC) {
         const int ne = min(EC, E1 - c0);
         __syncthreads();
-        chunk_prologue<H>(D, L, smem, c0, ne, dst, src, geom, W1, W2);
+        chunk_prologue<H, BF>(D, L, smem, c0, ne, dst, src, geom, W1, W2, W2T_h);
         if constexpr (BF) chunk_w_gemm_bf16<H>(D, L, smem, W3T_h);
         else chunk_w_gemm_f32<H>(D, L, smem, W3);
         for (int s = 0; s < D.n_slots[warp]; ++s) {
@@ -547,7 +587,8 @@ __device__ __forceinline__ void tp_bwd_path(const PathDesc& P, int u, int e, int
 #pragma unroll
     for (int c = 0; c < N3; ++c) g[c] = __ldg(gmr + c * P.m_mul);
     const float wv = s_w[e * Wpad + col];
-    const float* G = s_G + e * nG + P.g_off;
+    float G[((N1 * N3 + 3) / 4) * 4];
+    load_G<N1 * N3>(s_G + e * nG + P.g_off, G);
     float q[N1];
     float gw = 0.0f;
 #pragma unroll
@@ -675,6 +716,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 2)
 conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __restrict__ W2,
                 const float* __restrict__ W2T, const float* __restrict__ W3, const float* __restrict__ W3T,
                 const __nv_bfloat16* __restrict__ W3T_h, const __nv_bfloat16* __restrict__ W3_h,
+                const __nv_bfloat16* __restrict__ W2T_h, const __nv_bfloat16* __restrict__ W2_h,
                 int n_atoms,
                 int n_edges, const int* __restrict__ row_ptr, const int* __restrict__ dst,
                 const int* __restrict__ src, const float4* __restrict__ geom,
@@ -695,7 +737,7 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
     for (int c0 = E0; c0 < E1; c0 += EC) {
         const int ne = min(EC, E1 - c0);
         __syncthreads();
-        chunk_prologue<H>(D, L, smem, c0, ne, dst, src, geom, W1, W2);
+        chunk_prologue<H, BF>(D, L, smem, c0, ne, dst, src, geom, W1, W2, W2T_h);
         if constexpr (BF) chunk_w_gemm_bf16<H>(D, L, smem, W3T_h);
         else chunk_w_gemm_f32<H>(D, L, smem, W3);
         // E: per-edge adjoint of the tensor product
@@ -725,7 +767,19 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
         float* s_A2 = smem + L.A2;
         for (int i = t; i < H * EC; i += CONV_THREADS) s_gH[i] *= dsiluf_(s_A2[i]);
         __syncthreads();
-        {   // gA1 = (gA2 @ W2^T) * silu'(A1), stored over A2; W2T[j][k] = W2[k][j]
+        if constexpr (BF) {   // gA1 = (gA2 @ W2^T) * silu'(A1) on tensor cores, stored over A2
+            const int lane = t & 31, g = lane >> 2, tq = lane & 3;
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+            const int nt = warp;
+            if (nt < H / 8) hidden_mma<H>(s_gH, W2_h, c, nt);
+            __syncthreads();       // every read of A2 (the silu' above) is done
+            if (nt < H / 8) {
+                const int k = nt * 8 + 2 * tq;
+                const int o[4] = {k * EC + g, (k + 1) * EC + g, k * EC + g + 8, (k + 1) * EC + g + 8};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s_A2[o[q]] = c[q] * dsiluf_(s_A1[o[q]]);
+            }
+        } else {   // gA1 = (gA2 @ W2^T) * silu'(A1), stored over A2; W2T[j][k] = W2[k][j]
             float ga[(H / 4) * EC / CONV_THREADS > 0 ? (H / 4) * EC / CONV_THREADS : 1][4];
             int nq = 0;
             for (int idx = t; idx < (H / 4) * EC; idx += CONV_THREADS, ++nq) {
@@ -889,7 +943,7 @@ void launch_conv_fwd(const LayerDev& L, int H, sevennet_precision prec, int64_t 
     const size_t sm = smem_bytes(L.conv, H, false);
     const bool bf = prec == SEVENNET_BF16;
 #define SN_LF(HH, BB) conv_fwd_kernel<HH, BB><<<grid, CONV_THREADS, sm, st>>>(                     \
-        L.conv, L.mlp0, L.mlp1, L.mlp2, L.mlp2h, (int)n_atoms, (int)n_edges, row_ptr, dst, src, geom, x, m)
+        L.conv, L.mlp0, L.mlp1, L.mlp2, L.mlp2h, L.mlp1Th, (int)n_atoms, (int)n_edges, row_ptr, dst, src, geom, x, m)
     if (H == 64) { if (bf) SN_LF(64, true); else SN_LF(64, false); }
     else         { if (bf) SN_LF(32, true); else SN_LF(32, false); }
 #undef SN_LF
@@ -903,7 +957,8 @@ void launch_conv_bwd(const LayerDev& L, int H, sevennet_precision prec, int64_t 
     const size_t sm = smem_bytes(L.conv, H, true);
     const bool bf = prec == SEVENNET_BF16;
 #define SN_LB(HH, BB) conv_bwd_kernel<HH, BB><<<grid, CONV_THREADS, sm, st>>>(                     \
-        L.conv, L.mlp0, L.mlp1, L.mlp1T, L.mlp2, L.mlp2T, L.mlp2h, L.mlp2Th, (int)n_atoms,            \
+        L.conv, L.mlp0, L.mlp1, L.mlp1T, L.mlp2, L.mlp2T, L.mlp2h, L.mlp2Th, L.mlp1Th, L.mlp1h,       \
+        (int)n_atoms,                                                                                 \
         (int)n_edges, row_ptr, dst, src, geom, x, gm, gx, gd)
     if (H == 64) { if (bf) SN_LB(64, true); else SN_LB(64, false); }
     else         { if (bf) SN_LB(32, true); else SN_LB(32, false); }

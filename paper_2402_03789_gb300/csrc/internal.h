@@ -111,7 +111,7 @@ struct ConvDesc {
 struct GemmProb {
     const float* A;
     const float* B;            // [K][N] row-major FP32 (pre-scaled)
-    const __nv_bfloat16* Bh;   // [N][K] BF16 transpose, for the tensor-core path
+    const __nv_bfloat16* Bh;   // [N][K] BF16 transpose (hi), followed by the lo term at Bh + K*N
     float* C;
     int64_t n_atoms;
     int32_t R, K, N;
@@ -137,6 +137,8 @@ struct LayerDev {
     float* mlp0T = nullptr;  // [H][NB]
     float* mlp1T = nullptr;  // [H][H]
     float* mlp2T = nullptr;  // [W][H]
+    __nv_bfloat16* mlp1h = nullptr;   // [2][H][H] W2 as stored, hi then lo (B operand of gA2 @ W2^T)
+    __nv_bfloat16* mlp1Th = nullptr;  // [2][H][H] W2^T, hi then lo (B operand of H1 @ W2)
     __nv_bfloat16* mlp2h = nullptr;   // [W][H]  (N-major for mma B operand)
     __nv_bfloat16* mlp2Th = nullptr;  // [H][W]
     float* lin1[3] = {};  float* lin1T[3] = {};  __nv_bfloat16* lin1h[3] = {};  __nv_bfloat16* lin1Th[3] = {};

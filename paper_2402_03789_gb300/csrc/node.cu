@@ -90,7 +90,8 @@ gemm_f32_kernel(const GemmBatch batch) {
 // Tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulate).  64 x 64
 // tile, 8 warps as 4 (rows) x 2 (cols), each warp 16 rows x 32 cols.  A is
 // read as FP32 and rounded to BF16 in the fragment; B is the BF16 [N][K] copy.
-// Activations as hi + lo BF16 pairs (two MMAs), weights as one BF16 value.
+// Activations and weights both enter as hi + lo BF16 pairs; three MMAs
+// (hi*hi, lo*hi, hi*lo) keep about 16 mantissa bits of each operand.
 constexpr bool GEMM_SPLIT_ACT = true;
 
 __device__ __forceinline__ void split_bf16_n(float x, float y, uint32_t& hi, uint32_t& lo) {
@@ -144,12 +145,15 @@ gemm_bf16_kernel(const GemmBatch batch) {
         split_bf16_n(x1.x, x1.y, a[1], al[1]);
         split_bf16_n(x2.x, x2.y, a[2], al[2]);
         split_bf16_n(x3.x, x3.y, a[3], al[3]);
+        const int64_t lo_off = (int64_t)P.K * P.N / 2;     // in 32-bit words
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const uint32_t* brow = reinterpret_cast<const uint32_t*>(P.Bh + (int64_t)(nbase + j * 8 + g) * P.K);
-            uint32_t b[2] = {__ldg(brow + (kk >> 1)), __ldg(brow + ((kk + 8) >> 1))};
+            const uint32_t b[2] = {__ldg(brow + (kk >> 1)), __ldg(brow + ((kk + 8) >> 1))};
+            const uint32_t bl[2] = {__ldg(brow + lo_off + (kk >> 1)), __ldg(brow + lo_off + ((kk + 8) >> 1))};
             mma_bf16_n(c[j], a, b);
             if (GEMM_SPLIT_ACT) mma_bf16_n(c[j], al, b);
+            mma_bf16_n(c[j], a, bl);
         }
     }
 #pragma unroll
