@@ -39,6 +39,22 @@ int num_sms(int device) {
     return cached[device];
 }
 
+// ---------------------------------------------------------------- convolution set-up
+sevennet_status conv_configure_fwd(int H, size_t need);
+sevennet_status conv_configure_bwd(int H, size_t need);
+size_t conv_smem_bytes(const ConvDesc& D, int H, bool bwd);
+
+sevennet_status conv_configure(int H, const std::vector<LayerDev>& layers) {
+    size_t need_f = 0, need_b = 0;
+    for (const LayerDev& L : layers) {
+        need_f = std::max(need_f, conv_smem_bytes(L.conv, H, false));
+        need_b = std::max(need_b, conv_smem_bytes(L.conv, H, true));
+    }
+    SN_TRY(conv_configure_fwd(H, need_f));
+    SN_TRY(conv_configure_bwd(H, need_b));
+    return SEVENNET_OK;
+}
+
 // ---------------------------------------------------------------- diagnostics
 static std::atomic<int64_t> g_launch_count{0};
 
@@ -559,6 +575,17 @@ sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const do
             D.mul_in[l] = L.in_mul[l];
             D.x_off[l] = L.in_off[l];
             if (L.in_mul[l]) D.l1max = l;
+        }
+        D.kind = (t == 0 ? 1 : 0) | (L.last ? 2 : 0);
+        for (int l1 = 0; l1 <= 2; ++l1) {          // the kernels rely on this order
+            const PathList pl = path_list(l1, cfg->lmax, D.kind);
+            const int pb = path_begin(l1, cfg->lmax, D.kind);
+            for (int i = 0; i < pl.n; ++i)
+                if (pb + i >= D.n_paths || D.paths[pb + i].l1 != l1 || D.paths[pb + i].l2 != pl.l2[i] ||
+                    D.paths[pb + i].l3 != pl.l3[i]) {
+                    set_error("block %d: path table does not match the compile-time path list", t);
+                    return fail(SEVENNET_EINVAL);
+                }
         }
         D.W = col;
         D.Wpad = ((col + 3) & ~3) + 4;

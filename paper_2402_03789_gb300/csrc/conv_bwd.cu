@@ -1,0 +1,296 @@
+// Adjoint of the tensor-product convolution (Eqs. 5 and 8): given dE/dm,
+// dE/dx of the senders and dE/dd of every edge through the tensor product, the
+// radial MLP and the edge embedding.  Shared phases live in conv_common.cuh.
+#include "conv_common.cuh"
+
+#include <utility>
+
+namespace sn {
+
+// ------------------------------------------------------------- adjoint
+template <int L1, int L2, int L3>
+__device__ __forceinline__ void tp_bwd_path(const PathDesc& P, int u, int e, int v, const float* xv,
+                                            float* gx, float* gY, float* s_w, int Wpad,
+                                            const float* s_G, int nG,
+                                            const float* __restrict__ gm, int m_dim) {
+    constexpr int N1 = 2 * L1 + 1, N3 = 2 * L3 + 1;
+    const int col = P.col0 + u;
+    const float* gmr = gm + (size_t)v * m_dim + P.m_off + P.m_ch0 + u;
+    float g[N3];
+#pragma unroll
+    for (int c = 0; c < N3; ++c) g[c] = __ldg(gmr + c * P.m_mul);
+    const float wv = s_w[e * Wpad + col];
+    float G[((N1 * N3 + 3) / 4) * 4];
+    load_G<N1 * N3>(s_G + e * nG + P.g_off, G);
+    float q[N1];
+    float gw = 0.0f;
+#pragma unroll
+    for (int a = 0; a < N1; ++a) {
+        float tt = 0.0f;
+#pragma unroll
+        for (int c = 0; c < N3; ++c) tt = fmaf(G[a * N3 + c], g[c], tt);
+        q[a] = tt;
+        gw = fmaf(xv[a], tt, gw);
+        gx[a] = fmaf(wv, tt, gx[a]);
+    }
+    s_w[e * Wpad + col] = gw;        // dE/dw replaces w (same thread, same slot)
+    float wx[N1];
+#pragma unroll
+    for (int a = 0; a < N1; ++a) wx[a] = wv * xv[a];
+    CG<L1, L2, L3>::gY(wx, g, gY + L2 * L2);
+}
+
+template <typename F, int... Is>
+__device__ __forceinline__ void static_for_impl(F& f, std::integer_sequence<int, Is...>) {
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+template <int L1, int LMAX, int KIND>
+struct BlockPaths {
+    static constexpr PathList list = path_list(L1, LMAX, KIND);
+    static constexpr int begin = path_begin(L1, LMAX, KIND);
+};
+
+// All paths of one input irrep l1 for one edge: the channel loads, the path
+// descriptors and the CG code are resolved at compile time.
+template <int L1, int LMAX, int KIND>
+__device__ __forceinline__ void tp_bwd_l1(const ConvDesc& D, int lane, int e, int v, int sidx,
+                                          float* gY, float* s_w, const float* s_G,
+                                          const float* __restrict__ x,
+                                          const float* __restrict__ gm, float* __restrict__ gxo) {
+    using BP = BlockPaths<L1, LMAX, KIND>;
+    if constexpr (BP::list.n > 0) {
+        constexpr int N1 = 2 * L1 + 1;
+        const int mul = D.mul_in[L1];
+        const float* xr = x + (size_t)sidx * D.x_dim + D.x_off[L1];
+        float* gxr = gxo + (size_t)sidx * D.x_dim + D.x_off[L1];
+        for (int ub = 0; ub < mul; ub += 32) {
+            const int u = ub + lane;
+            float xv[N1], gx[N1];
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                xv[a] = __ldg(xr + a * mul + u);
+                gx[a] = 0.0f;
+            }
+            static_for<BP::list.n>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                tp_bwd_path<L1, BP::list.l2[i], BP::list.l3[i]>(D.paths[BP::begin + i], u, e, v, xv, gx, gY,
+                                                                s_w, D.Wpad, s_G, D.nG, gm, D.m_dim);
+            });
+#pragma unroll
+            for (int a = 0; a < N1; ++a) atomicAdd(gxr + a * mul + u, gx[a]);
+        }
+    }
+}
+
+// Phase E of the adjoint for every edge of the chunk (warp per edge).
+template <int LMAX, int KIND>
+__device__ __forceinline__ void tp_bwd_chunk(const ConvDesc& D, int ne, const int* s_dst, const int* s_src,
+                                             float* s_w, const float* s_G, float* s_gY,
+                                             const float* __restrict__ x, const float* __restrict__ gm,
+                                             float* __restrict__ gx) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int e = warp; e < ne; e += CONV_WARPS) {
+        const int v = s_dst[e], sidx = s_src[e];
+        float gY[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) gY[i] = 0.0f;
+        tp_bwd_l1<0, LMAX, KIND>(D, lane, e, v, sidx, gY, s_w, s_G, x, gm, gx);
+        tp_bwd_l1<1, LMAX, KIND>(D, lane, e, v, sidx, gY, s_w, s_G, x, gm, gx);
+        if constexpr (LMAX >= 2) tp_bwd_l1<2, LMAX, KIND>(D, lane, e, v, sidx, gY, s_w, s_G, x, gm, gx);
+        constexpr int NY = (LMAX + 1) * (LMAX + 1);
+#pragma unroll
+        for (int i = 0; i < NY; ++i) gY[i] = warp_sum(gY[i]);
+        if (lane < 9) {
+            float val = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NY; ++i) if (lane == i) val = gY[i];
+            s_gY[e * 9 + lane] = val;
+        }
+    }
+}
+
+template <int H, bool BF, int LMAX>
+__global__ void __launch_bounds__(CONV_THREADS, 2)
+conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __restrict__ W2,
+                const float* __restrict__ W2T, const float* __restrict__ W3, const float* __restrict__ W3T,
+                const __nv_bfloat16* __restrict__ W3T_h, const __nv_bfloat16* __restrict__ W3_h,
+                const __nv_bfloat16* __restrict__ W2T_h, const __nv_bfloat16* __restrict__ W2_h,
+                int n_atoms,
+                int n_edges, const int* __restrict__ row_ptr, const int* __restrict__ dst,
+                const int* __restrict__ src, const float4* __restrict__ geom,
+                const float* __restrict__ x, const float* __restrict__ gm,
+                float* __restrict__ gx, float* __restrict__ gd) {
+    extern __shared__ float4 smem4[];
+    float* smem = reinterpret_cast<float*>(smem4);
+    const ConvSmem L = conv_smem_layout(D.Wpad, H, D.nG, true);
+    __shared__ int s_range[2];
+    cta_range(n_atoms, n_edges, row_ptr, s_range);
+    const int v0 = s_range[0], v1 = s_range[1];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int E0 = row_ptr[v0], E1 = row_ptr[v1];
+    const int* s_src = reinterpret_cast<const int*>(smem + L.src);
+    const int* s_dst = reinterpret_cast<const int*>(smem + L.dst);
+    float* s_w = smem + L.w;
+    float* s_gY = smem + L.gY;
+    for (int c0 = E0; c0 < E1; c0 += EC) {
+        const int ne = min(EC, E1 - c0);
+        __syncthreads();
+        chunk_prologue<H, BF>(D, L, smem, c0, ne, dst, src, geom, W1, W2, W2T_h);
+        if constexpr (BF) chunk_w_gemm_bf16<H>(D, L, smem, W3T_h);
+        else chunk_w_gemm_f32<H>(D, L, smem, W3);
+        // E: per-edge adjoint of the tensor product (path lists fixed per block kind)
+        switch (D.kind) {
+            case 0: tp_bwd_chunk<LMAX, 0>(D, ne, s_dst, s_src, s_w, smem + L.G, s_gY, x, gm, gx); break;
+            case 1: tp_bwd_chunk<LMAX, 1>(D, ne, s_dst, s_src, s_w, smem + L.G, s_gY, x, gm, gx); break;
+            case 2: tp_bwd_chunk<LMAX, 2>(D, ne, s_dst, s_src, s_w, smem + L.G, s_gY, x, gm, gx); break;
+            default: tp_bwd_chunk<LMAX, 3>(D, ne, s_dst, s_src, s_w, smem + L.G, s_gY, x, gm, gx); break;
+        }
+        // F: dE/dH2 = dE/dw @ W3^T
+        if constexpr (BF) chunk_gw_gemm_bf16<H>(D, L, smem, W3_h);
+        else chunk_gw_gemm_f32<H>(D, L, smem, W3T);
+        // MLP adjoint: gA2 = gH2 * silu'(A2); gH1 = gA2 @ W2^T; gA1 = gH1 * silu'(A1); gB = gA1 @ W1^T
+        float* s_gH = smem + L.gH;
+        float* s_A1 = smem + L.A1;
+        float* s_A2 = smem + L.A2;
+        for (int i = t; i < H * EC; i += CONV_THREADS) s_gH[i] *= dsiluf_(s_A2[i]);
+        __syncthreads();
+        if constexpr (BF) {   // gA1 = (gA2 @ W2^T) * silu'(A1) on tensor cores, stored over A2
+            const int lane = t & 31, g = lane >> 2, tq = lane & 3;
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+            const int nt = warp;
+            if (nt < H / 8) hidden_mma<H>(s_gH, W2_h, c, nt);
+            __syncthreads();       // every read of A2 (the silu' above) is done
+            if (nt < H / 8) {
+                const int k = nt * 8 + 2 * tq;
+                const int o[4] = {k * EC + g, (k + 1) * EC + g, k * EC + g + 8, (k + 1) * EC + g + 8};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s_A2[o[q]] = c[q] * dsiluf_(s_A1[o[q]]);
+            }
+        } else {   // gA1 = (gA2 @ W2^T) * silu'(A1), stored over A2; W2T[j][k] = W2[k][j]
+            float ga[(H / 4) * EC / CONV_THREADS > 0 ? (H / 4) * EC / CONV_THREADS : 1][4];
+            int nq = 0;
+            for (int idx = t; idx < (H / 4) * EC; idx += CONV_THREADS, ++nq) {
+                const int kq = idx / EC, e = idx % EC;
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll 8
+                for (int j = 0; j < H; ++j) {
+                    const float4 b = __ldg(reinterpret_cast<const float4*>(W2T + j * H) + kq);
+                    const float a = s_gH[j * EC + e];
+                    a0 = fmaf(a, b.x, a0);
+                    a1 = fmaf(a, b.y, a1);
+                    a2 = fmaf(a, b.z, a2);
+                    a3 = fmaf(a, b.w, a3);
+                }
+                ga[nq][0] = a0; ga[nq][1] = a1; ga[nq][2] = a2; ga[nq][3] = a3;
+            }
+            __syncthreads();       // every read of A2 (the silu' above) is done
+            nq = 0;
+            for (int idx = t; idx < (H / 4) * EC; idx += CONV_THREADS, ++nq) {
+                const int kq = idx / EC, e = idx % EC;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int o = (4 * kq + q) * EC + e;
+                    s_A2[o] = ga[nq][q] * dsiluf_(s_A1[o]);
+                }
+            }
+        }
+        __syncthreads();
+        float* s_gB = smem + L.stage;              // [NB][EC]
+        for (int i = t; i < D.n_basis * EC; i += CONV_THREADS) {
+            const int n = i / EC, e = i % EC;
+            float a = 0.0f;
+#pragma unroll 8
+            for (int k = 0; k < H; ++k) a = fmaf(s_A2[k * EC + e], __ldg(W1 + n * H + k), a);
+            s_gB[i] = a;
+        }
+        __syncthreads();
+        // G: dE/dd = (dE/dr) u + (I - u u^T) dE/du / r
+        if (t < ne) {
+            const float4 g = geom[c0 + t];
+            const float r = g.w, inv = 1.0f / r;
+            const float ux = g.x * inv, uy = g.y * inv, uz = g.z * inv;
+            float env, denv;
+            envelope(D, r / D.r_cut, env, denv);
+            denv /= D.r_cut;
+            const float th = 3.14159265358979f * r / D.r_cut;
+            const float dth = 3.14159265358979f / D.r_cut;
+            float s1, c1;
+            sincosf(th, &s1, &c1);
+            float sm = 0.0f, sn = s1, cm = 1.0f, cn = c1;
+            const float k2 = 2.0f / D.r_cut;
+            float dEdr = 0.0f;
+            for (int n = 0; n < D.n_basis; ++n) {
+                const float nn = (float)(n + 1);
+                const float f = k2 * sn * inv;
+                const float df = k2 * (nn * dth * cn * inv - sn * inv * inv);
+                dEdr = fmaf(s_gB[n * EC + t], df * env + f * denv, dEdr);
+                const float ns = 2.0f * c1 * sn - sm;
+                const float nc = 2.0f * c1 * cn - cm;
+                sm = sn; sn = ns; cm = cn; cn = nc;
+            }
+            const float* gy = s_gY + t * 9;
+            const float s3 = 1.7320508075688772f, s15 = 3.872983346207417f, s5 = 2.23606797749979f;
+            float gux = s3 * gy[3], guy = s3 * gy[1], guz = s3 * gy[2];
+            if (D.lmax >= 2) {
+                gux += s15 * (uy * gy[4] + uz * gy[7] + ux * gy[8]);
+                guy += s15 * (ux * gy[4] + uz * gy[5] - uy * gy[8]);
+                guz += s15 * (uy * gy[5] + ux * gy[7]) + 3.0f * s5 * uz * gy[6];
+            }
+            const float dot = gux * ux + guy * uy + guz * uz;
+            float* o = gd + (size_t)(c0 + t) * 3;
+            o[0] += dEdr * ux + (gux - dot * ux) * inv;
+            o[1] += dEdr * uy + (guy - dot * uy) * inv;
+            o[2] += dEdr * uz + (guz - dot * uz) * inv;
+        }
+    }
+}
+
+// ------------------------------------------------------------- launcher
+sevennet_status conv_configure_bwd(int H, size_t need) {
+    static size_t granted[2][2] = {{0, 0}, {0, 0}};
+    const int hi = H == 64 ? 1 : 0;
+    if (H == 64) {
+        SN_TRY(conv_set_smem((const void*)conv_bwd_kernel<64, false, 1>, need, &granted[hi][0]));
+        SN_TRY(conv_set_smem((const void*)conv_bwd_kernel<64, true, 1>, need, &granted[hi][0]));
+        SN_TRY(conv_set_smem((const void*)conv_bwd_kernel<64, false, 2>, need, &granted[hi][0]));
+        SN_TRY(conv_set_smem((const void*)conv_bwd_kernel<64, true, 2>, need, &granted[hi][0]));
+    } else if (H == 32) {
+        SN_TRY(conv_set_smem((const void*)conv_bwd_kernel<32, false, 1>, need, &granted[hi][0]));
+        SN_TRY(conv_set_smem((const void*)conv_bwd_kernel<32, true, 1>, need, &granted[hi][0]));
+        SN_TRY(conv_set_smem((const void*)conv_bwd_kernel<32, false, 2>, need, &granted[hi][0]));
+        SN_TRY(conv_set_smem((const void*)conv_bwd_kernel<32, true, 2>, need, &granted[hi][0]));
+    } else {
+        set_error("radial MLP hidden width must be 32 or 64");
+        return SEVENNET_EINVAL;
+    }
+    return SEVENNET_OK;
+}
+
+void launch_conv_bwd(const LayerDev& L, int H, sevennet_precision prec, int64_t n_atoms,
+                     int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
+                     const float4* geom, const float* x, const float* gm, float* gx,
+                     float* gd, cudaStream_t st) {
+    const int grid = conv_grid(n_atoms);
+    const size_t sm = smem_bytes(L.conv, H, true);
+    const bool bf = prec == SEVENNET_BF16;
+#define SN_LB(HH, BB, LL) conv_bwd_kernel<HH, BB, LL><<<grid, CONV_THREADS, sm, st>>>(                 \
+        L.conv, L.mlp0, L.mlp1, L.mlp1T, L.mlp2, L.mlp2T, L.mlp2h, L.mlp2Th, L.mlp1Th, L.mlp1h,       \
+        (int)n_atoms, (int)n_edges, row_ptr, dst, src, geom, x, gm, gx, gd)
+    const int lm = L.conv.lmax;
+    if (H == 64) {
+        if (bf) { if (lm == 2) SN_LB(64, true, 2); else SN_LB(64, true, 1); }
+        else    { if (lm == 2) SN_LB(64, false, 2); else SN_LB(64, false, 1); }
+    } else {
+        if (bf) { if (lm == 2) SN_LB(32, true, 2); else SN_LB(32, true, 1); }
+        else    { if (lm == 2) SN_LB(32, false, 2); else SN_LB(32, false, 1); }
+    }
+#undef SN_LB
+}
+
+}  // namespace sn

@@ -1,3 +1,6 @@
+// Shared device code of the tensor-product convolution (forward: conv_fwd.cu,
+// adjoint: conv_bwd.cu).
+//
 // Tensor-product convolution of one interaction block and its adjoint.
 //
 // Forward (paper Eq. 3, Figure 2b; SevenNet-0 details Sec. 5.1):
@@ -19,6 +22,8 @@
 //      keeping the running sum of the current receiver in registers and writing
 //      it once when the receiver changes (segmented sum, no atomics);
 //      adjoint: each warp owns edges and walks all paths of that edge.
+#pragma once
+
 #include "internal.h"
 #include "cg_tables.cuh"
 
@@ -339,28 +344,27 @@ __device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem
                 s_H2[o[q]] = siluf_(c[q]);
             }
         }
-        __syncthreads();
-        return;
-    }
-    // A2 = H1 @ W2, H2 = silu(A2): each thread computes 4 hidden units of one edge
-    for (int idx = t; idx < (H / 4) * EC; idx += CONV_THREADS) {
-        const int jq = idx / EC, e = idx % EC;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    } else {
+        // A2 = H1 @ W2, H2 = silu(A2): each thread computes 4 hidden units of one edge
+        for (int idx = t; idx < (H / 4) * EC; idx += CONV_THREADS) {
+            const int jq = idx / EC, e = idx % EC;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll 8
-        for (int k = 0; k < H; ++k) {
-            const float4 b = __ldg(reinterpret_cast<const float4*>(W2 + k * H) + jq);
-            const float a = s_H1[k * EC + e];
-            a0 = fmaf(a, b.x, a0);
-            a1 = fmaf(a, b.y, a1);
-            a2 = fmaf(a, b.z, a2);
-            a3 = fmaf(a, b.w, a3);
-        }
-        const float av[4] = {a0, a1, a2, a3};
+            for (int k = 0; k < H; ++k) {
+                const float4 b = __ldg(reinterpret_cast<const float4*>(W2 + k * H) + jq);
+                const float a = s_H1[k * EC + e];
+                a0 = fmaf(a, b.x, a0);
+                a1 = fmaf(a, b.y, a1);
+                a2 = fmaf(a, b.z, a2);
+                a3 = fmaf(a, b.w, a3);
+            }
+            const float av[4] = {a0, a1, a2, a3};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int o = (4 * jq + q) * EC + e;
-            s_A2[o] = av[q];
-            s_H2[o] = siluf_(av[q]);
+            for (int q = 0; q < 4; ++q) {
+                const int o = (4 * jq + q) * EC + e;
+                s_A2[o] = av[q];
+                s_H2[o] = siluf_(av[q]);
+            }
         }
     }
     __syncthreads();
@@ -449,7 +453,6 @@ __device__ __forceinline__ void cta_range(int n_atoms, int n_edges, const int* _
     __syncthreads();
 }
 
-// ------------------------------------------------------------- forward
 // G matrix of one path into registers with 16-byte shared-memory loads
 // (every path's G starts on a 16-byte boundary).
 template <int NG>
@@ -465,186 +468,6 @@ __device__ __forceinline__ void load_G(const float* __restrict__ src, float* G) 
     }
 }
 
-template <int L1, int L2, int L3>
-__device__ __forceinline__ void tp_fwd_group(const PathDesc& P, int u, int c0, int ne,
-                                             const float* s_w, int Wpad, const float* s_G, int nG,
-                                             const int* s_src, const int* s_dst,
-                                             const int* __restrict__ row_ptr,
-                                             const float* __restrict__ x, int x_dim,
-                                             float* __restrict__ m, int m_dim) {
-    constexpr int N1 = 2 * L1 + 1, N3 = 2 * L3 + 1;
-    const int col = P.col0 + u;
-    const float* xb = x + P.x_off + u;
-    float* mb = m + P.m_off + P.m_ch0 + u;
-    float acc[N3];
-#pragma unroll
-    for (int c = 0; c < N3; ++c) acc[c] = 0.0f;
-    int cur = -1;
-    auto flush = [&](int v) {
-        float* mp = mb + (size_t)v * m_dim;
-        if (__ldg(row_ptr + v) >= c0) {
-#pragma unroll
-            for (int c = 0; c < N3; ++c) mp[c * P.m_mul] = acc[c];
-        } else {
-#pragma unroll
-            for (int c = 0; c < N3; ++c) mp[c * P.m_mul] += acc[c];
-        }
-    };
-    constexpr int PF = 4;       // edges whose gathers are in flight together
-    for (int e0 = 0; e0 < ne; e0 += PF) {
-        float xv[PF][N1];
-#pragma unroll
-        for (int q = 0; q < PF; ++q) {
-            const int e = min(e0 + q, ne - 1);
-            const float* xr = xb + (size_t)s_src[e] * x_dim;
-#pragma unroll
-            for (int a = 0; a < N1; ++a) xv[q][a] = __ldg(xr + a * P.mul);
-        }
-#pragma unroll
-        for (int q = 0; q < PF; ++q) {
-            const int e = e0 + q;
-            if (e >= ne) break;
-            const int v = s_dst[e];
-            if (v != cur) {
-                if (cur >= 0) flush(cur);
-                cur = v;
-#pragma unroll
-                for (int c = 0; c < N3; ++c) acc[c] = 0.0f;
-            }
-            const float wv = s_w[e * Wpad + col];
-            float G[((N1 * N3 + 3) / 4) * 4];
-            load_G<N1 * N3>(s_G + e * nG + P.g_off, G);
-#pragma unroll
-            for (int c = 0; c < N3; ++c) {
-                float tt = 0.0f;
-#pragma unroll
-                for (int a = 0; a < N1; ++a) tt = fmaf(xv[q][a], G[a * N3 + c], tt);
-                acc[c] = fmaf(wv, tt, acc[c]);
-            }
-        }
-    }
-    if (cur >= 0) flush(cur);
-}
-
-template <int H, bool BF>
-__global__ void __launch_bounds__(CONV_THREADS, 2)
-conv_fwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __restrict__ W2,
-                const float* __restrict__ W3, const __nv_bfloat16* __restrict__ W3T_h,
-                const __nv_bfloat16* __restrict__ W2T_h, int n_atoms, int n_edges,
-                const int* __restrict__ row_ptr, const int* __restrict__ dst,
-                const int* __restrict__ src, const float4* __restrict__ geom,
-                const float* __restrict__ x, float* __restrict__ m) {
-    extern __shared__ float4 smem4[];
-    float* smem = reinterpret_cast<float*>(smem4);
-    const ConvSmem L = conv_smem_layout(D.Wpad, H, D.nG, false);
-    __shared__ int s_range[2];
-    cta_range(n_atoms, n_edges, row_ptr, s_range);
-    const int v0 = s_range[0], v1 = s_range[1];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    // receivers without edges get zero messages
-    for (int v = v0 + warp; v < v1; v += CONV_WARPS) {
-        if (row_ptr[v] == row_ptr[v + 1]) {
-            for (int i = lane; i < D.m_dim; i += 32) m[(size_t)v * D.m_dim + i] = 0.0f;
-        }
-    }
-    const int E0 = row_ptr[v0], E1 = row_ptr[v1];
-    const int* s_src = reinterpret_cast<const int*>(smem + L.src);
-    const int* s_dst = reinterpret_cast<const int*>(smem + L.dst);
-    for (int c0 = E0; c0 < E1; c0 += EC) {
-        const int ne = min(EC, E1 - c0);
-        __syncthreads();
-        chunk_prologue<H, BF>(D, L, smem, c0, ne, dst, src, geom, W1, W2, W2T_h);
-        if constexpr (BF) chunk_w_gemm_bf16<H>(D, L, smem, W3T_h);
-        else chunk_w_gemm_f32<H>(D, L, smem, W3);
-        for (int s = 0; s < D.n_slots[warp]; ++s) {
-            const int g = D.slot_group[warp][s];
-            const PathDesc& P = D.paths[g >> 8];
-            const int u = (g & 255) * 32 + lane;
-            switch (P.kind) {
-#define SN_F(a, b, c) case coupling_kind(a, b, c):                                              \
-                tp_fwd_group<a, b, c>(P, u, c0, ne, smem + L.w, D.Wpad, smem + L.G, D.nG, s_src, \
-                                      s_dst, row_ptr, x, D.x_dim, m, D.m_dim); break;
-                SN_F(0, 0, 0) SN_F(0, 1, 1) SN_F(0, 2, 2)
-                SN_F(1, 0, 1) SN_F(1, 1, 0) SN_F(1, 1, 1) SN_F(1, 1, 2) SN_F(1, 2, 1) SN_F(1, 2, 2)
-                SN_F(2, 0, 2) SN_F(2, 1, 1) SN_F(2, 1, 2) SN_F(2, 2, 0) SN_F(2, 2, 1) SN_F(2, 2, 2)
-#undef SN_F
-                default: break;
-            }
-        }
-    }
-}
-
-// ------------------------------------------------------------- adjoint
-template <int L1, int L2, int L3>
-__device__ __forceinline__ void tp_bwd_path(const PathDesc& P, int u, int e, int v, const float* xv,
-                                            float* gx, float* gY, float* s_w, int Wpad,
-                                            const float* s_G, int nG,
-                                            const float* __restrict__ gm, int m_dim) {
-    constexpr int N1 = 2 * L1 + 1, N3 = 2 * L3 + 1;
-    const int col = P.col0 + u;
-    const float* gmr = gm + (size_t)v * m_dim + P.m_off + P.m_ch0 + u;
-    float g[N3];
-#pragma unroll
-    for (int c = 0; c < N3; ++c) g[c] = __ldg(gmr + c * P.m_mul);
-    const float wv = s_w[e * Wpad + col];
-    float G[((N1 * N3 + 3) / 4) * 4];
-    load_G<N1 * N3>(s_G + e * nG + P.g_off, G);
-    float q[N1];
-    float gw = 0.0f;
-#pragma unroll
-    for (int a = 0; a < N1; ++a) {
-        float tt = 0.0f;
-#pragma unroll
-        for (int c = 0; c < N3; ++c) tt = fmaf(G[a * N3 + c], g[c], tt);
-        q[a] = tt;
-        gw = fmaf(xv[a], tt, gw);
-        gx[a] = fmaf(wv, tt, gx[a]);
-    }
-    s_w[e * Wpad + col] = gw;        // dE/dw replaces w (same thread, same slot)
-    float wx[N1];
-#pragma unroll
-    for (int a = 0; a < N1; ++a) wx[a] = wv * xv[a];
-    CG<L1, L2, L3>::gY(wx, g, gY + L2 * L2);
-}
-
-template <int L1>
-__device__ __forceinline__ void tp_bwd_l1(const ConvDesc& D, int lane, int e, int v, int sidx,
-                                          float* gY, float* s_w, const float* s_G,
-                                          const float* __restrict__ x,
-                                          const float* __restrict__ gm, float* __restrict__ gxo) {
-    constexpr int N1 = 2 * L1 + 1;
-    const int mul = D.mul_in[L1];
-    const float* xr = x + (size_t)sidx * D.x_dim + D.x_off[L1];
-    float* gxr = gxo + (size_t)sidx * D.x_dim + D.x_off[L1];
-    for (int ub = 0; ub < mul; ub += 32) {
-        const int u = ub + lane;
-        float xv[N1], gx[N1];
-#pragma unroll
-        for (int a = 0; a < N1; ++a) {
-            xv[a] = __ldg(xr + a * mul + u);
-            gx[a] = 0.0f;
-        }
-        for (int p = D.pbeg[L1]; p < D.pend[L1]; ++p) {
-            const PathDesc& P = D.paths[p];
-            switch (P.l2 * 3 + P.l3) {
-#define SN_B(b, c)                                                                                  \
-                case (b) * 3 + (c):                                                                 \
-                    if constexpr (((L1 > b ? L1 - b : b - L1) <= c) && (c <= L1 + b) && c <= 2)     \
-                        tp_bwd_path<L1, b, c>(P, u, e, v, xv, gx, gY, s_w, D.Wpad, s_G, D.nG, gm,   \
-                                              D.m_dim);                                             \
-                    break;
-                SN_B(0, 0) SN_B(0, 1) SN_B(0, 2) SN_B(1, 0) SN_B(1, 1) SN_B(1, 2) SN_B(2, 0)
-                SN_B(2, 1) SN_B(2, 2)
-#undef SN_B
-                default: break;
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < N1; ++a) atomicAdd(gxr + a * mul + u, gx[a]);
-    }
-}
-
-// Phase F (FP32): gH2[k][e] = sum_c gw[e][c] W3T[c][k], split over two thread halves.
 template <int H>
 __device__ __forceinline__ void chunk_gw_gemm_f32(const ConvDesc& D, const ConvSmem& L, float* smem,
                                                   const float* __restrict__ W3T) {
@@ -711,224 +534,12 @@ __device__ __forceinline__ void chunk_gw_gemm_f32(const ConvDesc& D, const ConvS
     __syncthreads();
 }
 
-template <int H, bool BF>
-__global__ void __launch_bounds__(CONV_THREADS, 2)
-conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __restrict__ W2,
-                const float* __restrict__ W2T, const float* __restrict__ W3, const float* __restrict__ W3T,
-                const __nv_bfloat16* __restrict__ W3T_h, const __nv_bfloat16* __restrict__ W3_h,
-                const __nv_bfloat16* __restrict__ W2T_h, const __nv_bfloat16* __restrict__ W2_h,
-                int n_atoms,
-                int n_edges, const int* __restrict__ row_ptr, const int* __restrict__ dst,
-                const int* __restrict__ src, const float4* __restrict__ geom,
-                const float* __restrict__ x, const float* __restrict__ gm,
-                float* __restrict__ gx, float* __restrict__ gd) {
-    extern __shared__ float4 smem4[];
-    float* smem = reinterpret_cast<float*>(smem4);
-    const ConvSmem L = conv_smem_layout(D.Wpad, H, D.nG, true);
-    __shared__ int s_range[2];
-    cta_range(n_atoms, n_edges, row_ptr, s_range);
-    const int v0 = s_range[0], v1 = s_range[1];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int E0 = row_ptr[v0], E1 = row_ptr[v1];
-    const int* s_src = reinterpret_cast<const int*>(smem + L.src);
-    const int* s_dst = reinterpret_cast<const int*>(smem + L.dst);
-    float* s_w = smem + L.w;
-    float* s_gY = smem + L.gY;
-    for (int c0 = E0; c0 < E1; c0 += EC) {
-        const int ne = min(EC, E1 - c0);
-        __syncthreads();
-        chunk_prologue<H, BF>(D, L, smem, c0, ne, dst, src, geom, W1, W2, W2T_h);
-        if constexpr (BF) chunk_w_gemm_bf16<H>(D, L, smem, W3T_h);
-        else chunk_w_gemm_f32<H>(D, L, smem, W3);
-        // E: per-edge adjoint of the tensor product
-        for (int e = warp; e < ne; e += CONV_WARPS) {
-            const int v = s_dst[e], sidx = s_src[e];
-            float gY[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) gY[i] = 0.0f;
-            if (D.mul_in[0]) tp_bwd_l1<0>(D, lane, e, v, sidx, gY, s_w, smem + L.G, x, gm, gx);
-            if (D.mul_in[1]) tp_bwd_l1<1>(D, lane, e, v, sidx, gY, s_w, smem + L.G, x, gm, gx);
-            if (D.mul_in[2]) tp_bwd_l1<2>(D, lane, e, v, sidx, gY, s_w, smem + L.G, x, gm, gx);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) gY[i] = warp_sum(gY[i]);
-            if (lane < 9) {
-                float val = gY[0];
-#pragma unroll
-                for (int i = 1; i < 9; ++i) if (lane == i) val = gY[i];
-                s_gY[e * 9 + lane] = val;
-            }
-        }
-        // F: dE/dH2 = dE/dw @ W3^T
-        if constexpr (BF) chunk_gw_gemm_bf16<H>(D, L, smem, W3_h);
-        else chunk_gw_gemm_f32<H>(D, L, smem, W3T);
-        // MLP adjoint: gA2 = gH2 * silu'(A2); gH1 = gA2 @ W2^T; gA1 = gH1 * silu'(A1); gB = gA1 @ W1^T
-        float* s_gH = smem + L.gH;
-        float* s_A1 = smem + L.A1;
-        float* s_A2 = smem + L.A2;
-        for (int i = t; i < H * EC; i += CONV_THREADS) s_gH[i] *= dsiluf_(s_A2[i]);
-        __syncthreads();
-        if constexpr (BF) {   // gA1 = (gA2 @ W2^T) * silu'(A1) on tensor cores, stored over A2
-            const int lane = t & 31, g = lane >> 2, tq = lane & 3;
-            float c[4] = {0.f, 0.f, 0.f, 0.f};
-            const int nt = warp;
-            if (nt < H / 8) hidden_mma<H>(s_gH, W2_h, c, nt);
-            __syncthreads();       // every read of A2 (the silu' above) is done
-            if (nt < H / 8) {
-                const int k = nt * 8 + 2 * tq;
-                const int o[4] = {k * EC + g, (k + 1) * EC + g, k * EC + g + 8, (k + 1) * EC + g + 8};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) s_A2[o[q]] = c[q] * dsiluf_(s_A1[o[q]]);
-            }
-        } else {   // gA1 = (gA2 @ W2^T) * silu'(A1), stored over A2; W2T[j][k] = W2[k][j]
-            float ga[(H / 4) * EC / CONV_THREADS > 0 ? (H / 4) * EC / CONV_THREADS : 1][4];
-            int nq = 0;
-            for (int idx = t; idx < (H / 4) * EC; idx += CONV_THREADS, ++nq) {
-                const int kq = idx / EC, e = idx % EC;
-                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll 8
-                for (int j = 0; j < H; ++j) {
-                    const float4 b = __ldg(reinterpret_cast<const float4*>(W2T + j * H) + kq);
-                    const float a = s_gH[j * EC + e];
-                    a0 = fmaf(a, b.x, a0);
-                    a1 = fmaf(a, b.y, a1);
-                    a2 = fmaf(a, b.z, a2);
-                    a3 = fmaf(a, b.w, a3);
-                }
-                ga[nq][0] = a0; ga[nq][1] = a1; ga[nq][2] = a2; ga[nq][3] = a3;
-            }
-            __syncthreads();       // every read of A2 (the silu' above) is done
-            nq = 0;
-            for (int idx = t; idx < (H / 4) * EC; idx += CONV_THREADS, ++nq) {
-                const int kq = idx / EC, e = idx % EC;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int o = (4 * kq + q) * EC + e;
-                    s_A2[o] = ga[nq][q] * dsiluf_(s_A1[o]);
-                }
-            }
-        }
-        __syncthreads();
-        float* s_gB = smem + L.stage;              // [NB][EC]
-        for (int i = t; i < D.n_basis * EC; i += CONV_THREADS) {
-            const int n = i / EC, e = i % EC;
-            float a = 0.0f;
-#pragma unroll 8
-            for (int k = 0; k < H; ++k) a = fmaf(s_A2[k * EC + e], __ldg(W1 + n * H + k), a);
-            s_gB[i] = a;
-        }
-        __syncthreads();
-        // G: dE/dd = (dE/dr) u + (I - u u^T) dE/du / r
-        if (t < ne) {
-            const float4 g = geom[c0 + t];
-            const float r = g.w, inv = 1.0f / r;
-            const float ux = g.x * inv, uy = g.y * inv, uz = g.z * inv;
-            float env, denv;
-            envelope(D, r / D.r_cut, env, denv);
-            denv /= D.r_cut;
-            const float th = 3.14159265358979f * r / D.r_cut;
-            const float dth = 3.14159265358979f / D.r_cut;
-            float s1, c1;
-            sincosf(th, &s1, &c1);
-            float sm = 0.0f, sn = s1, cm = 1.0f, cn = c1;
-            const float k2 = 2.0f / D.r_cut;
-            float dEdr = 0.0f;
-            for (int n = 0; n < D.n_basis; ++n) {
-                const float nn = (float)(n + 1);
-                const float f = k2 * sn * inv;
-                const float df = k2 * (nn * dth * cn * inv - sn * inv * inv);
-                dEdr = fmaf(s_gB[n * EC + t], df * env + f * denv, dEdr);
-                const float ns = 2.0f * c1 * sn - sm;
-                const float nc = 2.0f * c1 * cn - cm;
-                sm = sn; sn = ns; cm = cn; cn = nc;
-            }
-            const float* gy = s_gY + t * 9;
-            const float s3 = 1.7320508075688772f, s15 = 3.872983346207417f, s5 = 2.23606797749979f;
-            float gux = s3 * gy[3], guy = s3 * gy[1], guz = s3 * gy[2];
-            if (D.lmax >= 2) {
-                gux += s15 * (uy * gy[4] + uz * gy[7] + ux * gy[8]);
-                guy += s15 * (ux * gy[4] + uz * gy[5] - uy * gy[8]);
-                guz += s15 * (uy * gy[5] + ux * gy[7]) + 3.0f * s5 * uz * gy[6];
-            }
-            const float dot = gux * ux + guy * uy + guz * uz;
-            float* o = gd + (size_t)(c0 + t) * 3;
-            o[0] += dEdr * ux + (gux - dot * ux) * inv;
-            o[1] += dEdr * uy + (guy - dot * uy) * inv;
-            o[2] += dEdr * uz + (guz - dot * uz) * inv;
-        }
-    }
-}
 
-// ------------------------------------------------------------- edge preparation
-__global__ void prep_dst_kernel(int64_t n, const int* __restrict__ row_ptr, int* __restrict__ dst) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
-    for (int e = row_ptr[v]; e < row_ptr[v + 1]; ++e) dst[e] = (int)v;
-}
-
-__global__ void prep_geom_kernel(int64_t E, const float* __restrict__ d, float4* __restrict__ geom) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E) return;
-    const float x = d[e * 3], y = d[e * 3 + 1], z = d[e * 3 + 2];
-    geom[e] = make_float4(x, y, z, sqrtf(x * x + y * y + z * z));
-}
-
-void conv_prepare_edges(int64_t n_atoms, int64_t n_edges, const int* row_ptr, const float* d, int* dst,
-                        float4* geom, cudaStream_t st) {
-    if (n_atoms > 0) prep_dst_kernel<<<(unsigned)((n_atoms + 255) / 256), 256, 0, st>>>(n_atoms, row_ptr, dst);
-    if (n_edges > 0) prep_geom_kernel<<<(unsigned)((n_edges + 255) / 256), 256, 0, st>>>(n_edges, d, geom);
-}
-
-// ------------------------------------------------------------- launchers
-static size_t smem_bytes(const ConvDesc& D, int H, bool bwd) {
+static inline size_t smem_bytes(const ConvDesc& D, int H, bool bwd) {
     return (size_t)conv_smem_layout(D.Wpad, H, D.nG, bwd).total * sizeof(float);
 }
 
-// Opt the convolution kernels into the shared memory the model's blocks need.
-sevennet_status conv_configure(int H, const std::vector<LayerDev>& layers) {
-    int dev = 0;
-    SN_CUDA(cudaGetDevice(&dev));
-    int optin = 0;
-    SN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    size_t need_f = 0, need_b = 0;
-    for (const LayerDev& L : layers) {
-        need_f = std::max(need_f, smem_bytes(L.conv, H, false));
-        need_b = std::max(need_b, smem_bytes(L.conv, H, true));
-    }
-    // never lower a limit another model of the process relies on
-    static size_t granted[2][2] = {{0, 0}, {0, 0}};
-    const int hi = (H == 64) ? 1 : 0;
-    need_f = std::max(need_f, granted[hi][0]);
-    need_b = std::max(need_b, granted[hi][1]);
-    granted[hi][0] = need_f;
-    granted[hi][1] = need_b;
-    auto set = [&](const void* fn, size_t need) -> sevennet_status {
-        cudaFuncAttributes a{};
-        SN_CUDA(cudaFuncGetAttributes(&a, fn));
-        SN_CHECK(need + a.sharedSizeBytes <= (size_t)optin, SEVENNET_EINVAL,
-                 "convolution needs %zu bytes of shared memory, the device allows %d", need, optin);
-        SN_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
-        return SEVENNET_OK;
-    };
-    if (H == 64) {
-        SN_TRY(set((const void*)conv_fwd_kernel<64, false>, need_f));
-        SN_TRY(set((const void*)conv_bwd_kernel<64, false>, need_b));
-        SN_TRY(set((const void*)conv_fwd_kernel<64, true>, need_f));
-        SN_TRY(set((const void*)conv_bwd_kernel<64, true>, need_b));
-    } else if (H == 32) {
-        SN_TRY(set((const void*)conv_fwd_kernel<32, false>, need_f));
-        SN_TRY(set((const void*)conv_bwd_kernel<32, false>, need_b));
-        SN_TRY(set((const void*)conv_fwd_kernel<32, true>, need_f));
-        SN_TRY(set((const void*)conv_bwd_kernel<32, true>, need_b));
-    } else {
-        set_error("radial MLP hidden width must be 32 or 64");
-        return SEVENNET_EINVAL;
-    }
-    return SEVENNET_OK;
-}
-
-size_t conv_smem_need(const ConvDesc& D, int H) { return smem_bytes(D, H, true); }
-
-static int conv_grid(int64_t n_atoms) {
+static inline int conv_grid(int64_t n_atoms) {
     int dev = 0;
     cudaGetDevice(&dev);
     int g = 2 * num_sms(dev);                 // two CTAs per SM
@@ -936,33 +547,20 @@ static int conv_grid(int64_t n_atoms) {
     return g;
 }
 
-void launch_conv_fwd(const LayerDev& L, int H, sevennet_precision prec, int64_t n_atoms,
-                     int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
-                     const float4* geom, const float* x, float* m, cudaStream_t st) {
-    const int grid = conv_grid(n_atoms);
-    const size_t sm = smem_bytes(L.conv, H, false);
-    const bool bf = prec == SEVENNET_BF16;
-#define SN_LF(HH, BB) conv_fwd_kernel<HH, BB><<<grid, CONV_THREADS, sm, st>>>(                     \
-        L.conv, L.mlp0, L.mlp1, L.mlp2, L.mlp2h, L.mlp1Th, (int)n_atoms, (int)n_edges, row_ptr, dst, src, geom, x, m)
-    if (H == 64) { if (bf) SN_LF(64, true); else SN_LF(64, false); }
-    else         { if (bf) SN_LF(32, true); else SN_LF(32, false); }
-#undef SN_LF
-}
-
-void launch_conv_bwd(const LayerDev& L, int H, sevennet_precision prec, int64_t n_atoms,
-                     int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
-                     const float4* geom, const float* x, const float* gm, float* gx,
-                     float* gd, cudaStream_t st) {
-    const int grid = conv_grid(n_atoms);
-    const size_t sm = smem_bytes(L.conv, H, true);
-    const bool bf = prec == SEVENNET_BF16;
-#define SN_LB(HH, BB) conv_bwd_kernel<HH, BB><<<grid, CONV_THREADS, sm, st>>>(                     \
-        L.conv, L.mlp0, L.mlp1, L.mlp1T, L.mlp2, L.mlp2T, L.mlp2h, L.mlp2Th, L.mlp1Th, L.mlp1h,       \
-        (int)n_atoms,                                                                                 \
-        (int)n_edges, row_ptr, dst, src, geom, x, gm, gx, gd)
-    if (H == 64) { if (bf) SN_LB(64, true); else SN_LB(64, false); }
-    else         { if (bf) SN_LB(32, true); else SN_LB(32, false); }
-#undef SN_LB
+// Opt a kernel into `need` bytes of dynamic shared memory (never lowering a
+// limit granted before in this process).
+static inline sevennet_status conv_set_smem(const void* fn, size_t need, size_t* granted) {
+    int dev = 0, optin = 0;
+    SN_CUDA(cudaGetDevice(&dev));
+    SN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    need = need > *granted ? need : *granted;
+    cudaFuncAttributes a{};
+    SN_CUDA(cudaFuncGetAttributes(&a, fn));
+    SN_CHECK(need + a.sharedSizeBytes <= (size_t)optin, SEVENNET_EINVAL,
+             "convolution needs %zu bytes of shared memory, the device allows %d", need, optin);
+    SN_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+    *granted = need;
+    return SEVENNET_OK;
 }
 
 }  // namespace sn

@@ -71,6 +71,35 @@ __host__ __device__ constexpr int coupling_kind(int l1, int l2, int l3) {
     return -1;
 }
 
+// Path set of a block, known at compile time from (l1, lmax, kind): the
+// couplings (l1, l2, l3) with |l1-l2| <= l3 <= min(l1+l2, lmax), l2 <= lmax;
+// the first block has l1 = 0 only, the last keeps l3 = 0 only.  Same order as
+// the block's runtime path table.
+struct PathList {
+    int n;
+    int l2[9];
+    int l3[9];
+};
+
+__host__ __device__ constexpr PathList path_list(int l1, int lmax, int kind) {
+    PathList p{0, {0, 0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0, 0, 0, 0}};
+    if (((kind & 1) && l1 != 0) || l1 > lmax) return p;
+    for (int l2 = 0; l2 <= lmax; ++l2)
+        for (int l3 = (l1 > l2 ? l1 - l2 : l2 - l1); l3 <= (l1 + l2 < lmax ? l1 + l2 : lmax); ++l3) {
+            if ((kind & 2) && l3 != 0) continue;
+            p.l2[p.n] = l2;
+            p.l3[p.n] = l3;
+            ++p.n;
+        }
+    return p;
+}
+
+__host__ __device__ constexpr int path_begin(int l1, int lmax, int kind) {
+    int s = 0;
+    for (int l = 0; l < l1; ++l) s += path_list(l, lmax, kind).n;
+    return s;
+}
+
 struct PathDesc {
     int32_t l1, l2, l3, kind;
     int32_t mul;      // channels of the path (= multiplicity of l1 in the block input)
@@ -97,6 +126,7 @@ struct ConvDesc {
     int32_t mul_in[3];  // multiplicity of l in the block input (0 = absent)
     int32_t x_off[3];
     int32_t pbeg[3], pend[3];   // paths with l1 = l occupy [pbeg, pend)
+    int32_t kind;               // bit 0: first block (input mul0 x 0e), bit 1: last block (l3 = 0)
     float r_cut;
     float env_a, env_b, env_c;  // envelope coefficients
     int32_t poly_p;
