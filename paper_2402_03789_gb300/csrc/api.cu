@@ -227,15 +227,30 @@ static sevennet_status upload_linear(sevennet_model* M, const double* w, int row
     return SEVENNET_OK;
 }
 
-// Balanced assignment of 32-channel path groups to warps (longest first).
-static bool assign_slots(ConvDesc& D) {
-    struct G { int p, ub, cost; };
-    std::vector<G> gs;
-    for (int p = 0; p < D.n_paths; ++p) {
-        const PathDesc& P = D.paths[p];
-        const int n1 = 2 * P.l1 + 1, n3 = 2 * P.l3 + 1;
-        for (int ub = 0; ub < P.mul / 32; ++ub) gs.push_back({p, ub, n1 * n3 + n1 + 3});
+// Forward work groups: one path and CPL in {1, 2, 4} channels per lane (the
+// largest CPL that still leaves at least 1.5 groups per warp), assigned to
+// warps longest first.  Encoding: (path << 8) | (channel block << 2) | log2 CPL.
+static bool assign_slots(ConvDesc& D, int H) {
+    struct G { int p, ub, lc, cost; };
+    auto groups_for = [&](int cap, std::vector<G>* out) {
+        int n = 0;
+        for (int p = 0; p < D.n_paths; ++p) {
+            const PathDesc& P = D.paths[p];
+            int cpl = std::min(cap, P.mul / 32), lc = 0;
+            while ((1 << (lc + 1)) <= cpl && fwd_cpl_compiled(H, P.l1, 1 << (lc + 1))) ++lc;
+            cpl = 1 << lc;
+            const int n1 = 2 * P.l1 + 1, n3 = 2 * P.l3 + 1;
+            for (int ub = 0; ub < P.mul / (32 * cpl); ++ub, ++n)
+                if (out) out->push_back({p, ub, lc, cpl * (n1 * n3 + n3 + n1) + 4});
+        }
+        return n;
+    };
+    int cap = 1;
+    for (int c : {4, 2}) {
+        if (groups_for(c, nullptr) * 2 >= 3 * CONV_WARPS) { cap = c; break; }
     }
+    std::vector<G> gs;
+    groups_for(cap, &gs);
     std::stable_sort(gs.begin(), gs.end(), [](const G& a, const G& b) { return a.cost > b.cost; });
     int load[CONV_WARPS] = {0};
     for (int w = 0; w < CONV_WARPS; ++w) D.n_slots[w] = 0;
@@ -243,8 +258,8 @@ static bool assign_slots(ConvDesc& D) {
         int best = -1;
         for (int w = 0; w < CONV_WARPS; ++w)
             if (D.n_slots[w] < MAX_SLOTS && (best < 0 || load[w] < load[best])) best = w;
-        if (best < 0) return false;
-        D.slot_group[best][D.n_slots[best]++] = (int16_t)((g.p << 8) | g.ub);
+        if (best < 0 || g.ub > 63) return false;
+        D.slot_group[best][D.n_slots[best]++] = (int16_t)((g.p << 8) | (g.ub << 2) | g.lc);
         load[best] += g.cost;
     }
     return true;
@@ -601,7 +616,8 @@ sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const do
         D.env_b = (float)(p * (p + 2.0));
         D.env_c = (float)(p * (p + 1.0) / 2.0);
         D.poly_p = cfg->poly_p;
-        if (!assign_slots(D)) { set_error("block %d: too many channel groups", t); return fail(SEVENNET_EINVAL); }
+        // the H = 32 kernels take one channel per lane
+        if (!assign_slots(D, H)) { set_error("block %d: too many channel groups", t); return fail(SEVENNET_EINVAL); }
         // weights
         const std::string pre = "L" + std::to_string(t) + ".";
         sevennet_status s;

@@ -8,36 +8,40 @@
 namespace sn {
 
 // ------------------------------------------------------------- adjoint
-template <int L1, int L2, int L3>
-__device__ __forceinline__ void tp_bwd_path(const PathDesc& P, int u, int e, int v, const float* xv,
-                                            float* gx, float* gY, float* s_w, int Wpad,
+// One path of one edge for CPL channels per lane (channels u0 + 32 k): the
+// G matrix and the address arithmetic serve all of them.
+template <int L1, int L2, int L3, int CPL>
+__device__ __forceinline__ void tp_bwd_path(const PathDesc& P, int u0, int e, int v, const float (*xv)[2 * L1 + 1],
+                                            float (*gx)[2 * L1 + 1], float* gY, float* s_w, int Wpad,
                                             const float* s_G, int nG,
                                             const float* __restrict__ gm, int m_dim) {
     constexpr int N1 = 2 * L1 + 1, N3 = 2 * L3 + 1;
-    const int col = P.col0 + u;
-    const float* gmr = gm + (size_t)v * m_dim + P.m_off + P.m_ch0 + u;
-    float g[N3];
+    float* wr = s_w + e * Wpad + P.col0 + u0;
+    const float* gmr = gm + (size_t)v * m_dim + P.m_off + P.m_ch0 + u0;
+    float g[CPL][N3];
 #pragma unroll
-    for (int c = 0; c < N3; ++c) g[c] = __ldg(gmr + c * P.m_mul);
-    const float wv = s_w[e * Wpad + col];
+    for (int k = 0; k < CPL; ++k)
+#pragma unroll
+        for (int c = 0; c < N3; ++c) g[k][c] = __ldg(gmr + c * P.m_mul + 32 * k);
     float G[((N1 * N3 + 3) / 4) * 4];
     load_G<N1 * N3>(s_G + e * nG + P.g_off, G);
-    float q[N1];
-    float gw = 0.0f;
 #pragma unroll
-    for (int a = 0; a < N1; ++a) {
-        float tt = 0.0f;
+    for (int k = 0; k < CPL; ++k) {
+        const float wv = wr[32 * k];
+        float gw = 0.0f;
+        float wx[N1];
 #pragma unroll
-        for (int c = 0; c < N3; ++c) tt = fmaf(G[a * N3 + c], g[c], tt);
-        q[a] = tt;
-        gw = fmaf(xv[a], tt, gw);
-        gx[a] = fmaf(wv, tt, gx[a]);
+        for (int a = 0; a < N1; ++a) {
+            float tt = 0.0f;
+#pragma unroll
+            for (int c = 0; c < N3; ++c) tt = fmaf(G[a * N3 + c], g[k][c], tt);
+            gw = fmaf(xv[k][a], tt, gw);
+            gx[k][a] = fmaf(wv, tt, gx[k][a]);
+            wx[a] = wv * xv[k][a];
+        }
+        wr[32 * k] = gw;             // dE/dw replaces w (same thread, same slot)
+        CG<L1, L2, L3>::gY(wx, g[k], gY + L2 * L2);
     }
-    s_w[e * Wpad + col] = gw;        // dE/dw replaces w (same thread, same slot)
-    float wx[N1];
-#pragma unroll
-    for (int a = 0; a < N1; ++a) wx[a] = wv * xv[a];
-    CG<L1, L2, L3>::gY(wx, g, gY + L2 * L2);
 }
 
 template <typename F, int... Is>
@@ -56,40 +60,61 @@ struct BlockPaths {
     static constexpr int begin = path_begin(L1, LMAX, KIND);
 };
 
-// All paths of one input irrep l1 for one edge: the channel loads, the path
-// descriptors and the CG code are resolved at compile time.
-template <int L1, int LMAX, int KIND>
+// All paths of one input irrep l1 for one edge, CPL channels per lane: the
+// channel loads, the path descriptors and the CG code resolve at compile time.
+template <int L1, int LMAX, int KIND, int CPL>
+__device__ __forceinline__ void tp_bwd_block(const ConvDesc& D, int u0, int e, int v, int sidx, float* gY,
+                                             float* s_w, const float* s_G, const float* __restrict__ x,
+                                             const float* __restrict__ gm, float* __restrict__ gxo) {
+    using BP = BlockPaths<L1, LMAX, KIND>;
+    constexpr int N1 = 2 * L1 + 1;
+    const int mul = D.mul_in[L1];
+    const float* xr = x + (size_t)sidx * D.x_dim + D.x_off[L1] + u0;
+    float* gxr = gxo + (size_t)sidx * D.x_dim + D.x_off[L1] + u0;
+    float xv[CPL][N1], gx[CPL][N1];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k)
+#pragma unroll
+        for (int a = 0; a < N1; ++a) {
+            xv[k][a] = __ldg(xr + a * mul + 32 * k);
+            gx[k][a] = 0.0f;
+        }
+    static_for<BP::list.n>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        tp_bwd_path<L1, BP::list.l2[i], BP::list.l3[i], CPL>(D.paths[BP::begin + i], u0, e, v, xv, gx, gY,
+                                                             s_w, D.Wpad, s_G, D.nG, gm, D.m_dim);
+    });
+#pragma unroll
+    for (int k = 0; k < CPL; ++k)
+#pragma unroll
+        for (int a = 0; a < N1; ++a) atomicAdd(gxr + a * mul + 32 * k, gx[k][a]);
+}
+
+template <int L1, int LMAX, int KIND, int MAXC>
 __device__ __forceinline__ void tp_bwd_l1(const ConvDesc& D, int lane, int e, int v, int sidx,
                                           float* gY, float* s_w, const float* s_G,
                                           const float* __restrict__ x,
                                           const float* __restrict__ gm, float* __restrict__ gxo) {
-    using BP = BlockPaths<L1, LMAX, KIND>;
-    if constexpr (BP::list.n > 0) {
-        constexpr int N1 = 2 * L1 + 1;
+    if constexpr (BlockPaths<L1, LMAX, KIND>::list.n > 0) {
         const int mul = D.mul_in[L1];
-        const float* xr = x + (size_t)sidx * D.x_dim + D.x_off[L1];
-        float* gxr = gxo + (size_t)sidx * D.x_dim + D.x_off[L1];
-        for (int ub = 0; ub < mul; ub += 32) {
-            const int u = ub + lane;
-            float xv[N1], gx[N1];
-#pragma unroll
-            for (int a = 0; a < N1; ++a) {
-                xv[a] = __ldg(xr + a * mul + u);
-                gx[a] = 0.0f;
+        for (int ub = 0; ub < mul;) {
+            const int left = (mul - ub) / 32;
+            if (MAXC >= 4 && left >= 4) {
+                tp_bwd_block<L1, LMAX, KIND, (MAXC >= 4 ? 4 : 1)>(D, ub + lane, e, v, sidx, gY, s_w, s_G, x, gm, gxo);
+                ub += 128;
+            } else if (MAXC >= 2 && left >= 2) {
+                tp_bwd_block<L1, LMAX, KIND, (MAXC >= 2 ? 2 : 1)>(D, ub + lane, e, v, sidx, gY, s_w, s_G, x, gm, gxo);
+                ub += 64;
+            } else {
+                tp_bwd_block<L1, LMAX, KIND, 1>(D, ub + lane, e, v, sidx, gY, s_w, s_G, x, gm, gxo);
+                ub += 32;
             }
-            static_for<BP::list.n>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                tp_bwd_path<L1, BP::list.l2[i], BP::list.l3[i]>(D.paths[BP::begin + i], u, e, v, xv, gx, gY,
-                                                                s_w, D.Wpad, s_G, D.nG, gm, D.m_dim);
-            });
-#pragma unroll
-            for (int a = 0; a < N1; ++a) atomicAdd(gxr + a * mul + u, gx[a]);
         }
     }
 }
 
 // Phase E of the adjoint for every edge of the chunk (warp per edge).
-template <int LMAX, int KIND>
+template <int LMAX, int KIND, int MAXC>
 __device__ __forceinline__ void tp_bwd_chunk(const ConvDesc& D, int ne, const int* s_dst, const int* s_src,
                                              float* s_w, const float* s_G, float* s_gY,
                                              const float* __restrict__ x, const float* __restrict__ gm,
@@ -100,9 +125,9 @@ __device__ __forceinline__ void tp_bwd_chunk(const ConvDesc& D, int ne, const in
         float gY[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) gY[i] = 0.0f;
-        tp_bwd_l1<0, LMAX, KIND>(D, lane, e, v, sidx, gY, s_w, s_G, x, gm, gx);
-        tp_bwd_l1<1, LMAX, KIND>(D, lane, e, v, sidx, gY, s_w, s_G, x, gm, gx);
-        if constexpr (LMAX >= 2) tp_bwd_l1<2, LMAX, KIND>(D, lane, e, v, sidx, gY, s_w, s_G, x, gm, gx);
+        tp_bwd_l1<0, LMAX, KIND, MAXC>(D, lane, e, v, sidx, gY, s_w, s_G, x, gm, gx);
+        tp_bwd_l1<1, LMAX, KIND, MAXC>(D, lane, e, v, sidx, gY, s_w, s_G, x, gm, gx);
+        if constexpr (LMAX >= 2) tp_bwd_l1<2, LMAX, KIND, MAXC>(D, lane, e, v, sidx, gY, s_w, s_G, x, gm, gx);
         constexpr int NY = (LMAX + 1) * (LMAX + 1);
 #pragma unroll
         for (int i = 0; i < NY; ++i) gY[i] = warp_sum(gY[i]);
@@ -138,18 +163,23 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
     const int* s_dst = reinterpret_cast<const int*>(smem + L.dst);
     float* s_w = smem + L.w;
     float* s_gY = smem + L.gY;
+    EdgePrefetch pf;
+    pf.fetch(E0, E1, dst, src, geom, row_ptr);
     for (int c0 = E0; c0 < E1; c0 += EC) {
         const int ne = min(EC, E1 - c0);
         __syncthreads();
-        chunk_prologue<H, BF>(D, L, smem, c0, ne, dst, src, geom, W1, W2, W2T_h);
+        chunk_prologue<H, BF>(D, L, smem, c0, ne, pf, W1, W2, W2T_h);
+        pf.fetch(c0 + EC, E1, dst, src, geom, row_ptr);   // next chunk's edges, in flight meanwhile
         if constexpr (BF) chunk_w_gemm_bf16<H>(D, L, smem, W3T_h);
         else chunk_w_gemm_f32<H>(D, L, smem, W3);
-        // E: per-edge adjoint of the tensor product (path lists fixed per block kind)
+        // E: per-edge adjoint of the tensor product (path lists fixed per block kind);
+        // the H = 32 kernels (small models) take one channel per lane
+        constexpr int MAXC = H == 64 ? 2 : 1;
         switch (D.kind) {
-            case 0: tp_bwd_chunk<LMAX, 0>(D, ne, s_dst, s_src, s_w, smem + L.G, s_gY, x, gm, gx); break;
-            case 1: tp_bwd_chunk<LMAX, 1>(D, ne, s_dst, s_src, s_w, smem + L.G, s_gY, x, gm, gx); break;
-            case 2: tp_bwd_chunk<LMAX, 2>(D, ne, s_dst, s_src, s_w, smem + L.G, s_gY, x, gm, gx); break;
-            default: tp_bwd_chunk<LMAX, 3>(D, ne, s_dst, s_src, s_w, smem + L.G, s_gY, x, gm, gx); break;
+            case 0: tp_bwd_chunk<LMAX, 0, MAXC>(D, ne, s_dst, s_src, s_w, smem + L.G, s_gY, x, gm, gx); break;
+            case 1: tp_bwd_chunk<LMAX, 1, MAXC>(D, ne, s_dst, s_src, s_w, smem + L.G, s_gY, x, gm, gx); break;
+            case 2: tp_bwd_chunk<LMAX, 2, MAXC>(D, ne, s_dst, s_src, s_w, smem + L.G, s_gY, x, gm, gx); break;
+            default: tp_bwd_chunk<LMAX, 3, MAXC>(D, ne, s_dst, s_src, s_w, smem + L.G, s_gY, x, gm, gx); break;
         }
         // F: dE/dH2 = dE/dw @ W3^T
         if constexpr (BF) chunk_gw_gemm_bf16<H>(D, L, smem, W3_h);

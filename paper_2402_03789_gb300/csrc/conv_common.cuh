@@ -34,7 +34,7 @@ constexpr int DCOLS = 512;    // columns per pass of phase D
 constexpr int CS = 32;        // column slice of phase F (adjoint W3 product)
 
 struct ConvSmem {
-    int w, stage, A1, A2, H2, gH, G, Y, B, gY, src, dst, total;
+    int w, stage, A1, A2, H2, gH, G, Y, B, gY, src, dst, first, total;
 };
 
 __host__ __device__ inline int rup4(int x) { return (x + 3) & ~3; }
@@ -54,6 +54,7 @@ __host__ __device__ inline ConvSmem conv_smem_layout(int Wpad, int H, int nG, bo
     s.gY = o;    o += bwd ? EC * 9 : 0;
     s.src = o;   o += EC;
     s.dst = o;   o += EC;
+    s.first = o; o += EC;
     s.total = o;
     return s;
 }
@@ -153,66 +154,69 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// The reduction order inside one MMA k step is free, so the BF16 products
+// below permute k identically in the A and B fragments: lane (g, tq) owns the
+// 32-bit words [tq * 2 KSN, (tq + 1) * 2 KSN) of every B row, which makes its B
+// operand two contiguous 16-byte loads; k step ks then uses words
+// w0 = tq * 2 KSN + 2 ks (first half of the fragment) and w0 + 1 (second half).
+
 // Phase D (BF16): w[e][c] = sum_k H2[k][e] W3[k][c]; B operand W3T [W][H] (bf16).
+// Each warp loads the B fragments of four n tiles at once.
 template <int H>
 __device__ __forceinline__ void chunk_w_gemm_bf16(const ConvDesc& D, const ConvSmem& L, float* smem,
                                                   const __nv_bfloat16* __restrict__ W3T) {
-    constexpr int KSN = H / 16;
-    constexpr int MT = EC / 16;
+    constexpr int KSN = H / 16;                // k steps (4 or 2)
+    constexpr int NV = KSN / 2;                // 16-byte loads per lane and n tile
+    constexpr int BATCH = 4;
+    static_assert(EC == 16, "one m tile of edges");
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tq = lane & 3;
     const float* s_H2 = smem + L.H2;
     float* s_w = smem + L.w;
-    uint32_t af[MT][KSN][4], al[MT][KSN][4];
+    uint32_t af[KSN][4], al[KSN][4];
 #pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-        for (int ks = 0; ks < KSN; ++ks) {
-            const int k0 = ks * 16 + 2 * tq, e0 = mt * 16 + g;
-            split_bf16(s_H2[k0 * EC + e0], s_H2[(k0 + 1) * EC + e0], af[mt][ks][0], al[mt][ks][0]);
-            split_bf16(s_H2[k0 * EC + e0 + 8], s_H2[(k0 + 1) * EC + e0 + 8], af[mt][ks][1], al[mt][ks][1]);
-            split_bf16(s_H2[(k0 + 8) * EC + e0], s_H2[(k0 + 9) * EC + e0], af[mt][ks][2], al[mt][ks][2]);
-            split_bf16(s_H2[(k0 + 8) * EC + e0 + 8], s_H2[(k0 + 9) * EC + e0 + 8], af[mt][ks][3], al[mt][ks][3]);
-        }
+    for (int ks = 0; ks < KSN; ++ks) {
+        const int k0 = 2 * (tq * 2 * KSN + 2 * ks), k1 = k0 + 2;
+        split_bf16(s_H2[k0 * EC + g], s_H2[(k0 + 1) * EC + g], af[ks][0], al[ks][0]);
+        split_bf16(s_H2[k0 * EC + g + 8], s_H2[(k0 + 1) * EC + g + 8], af[ks][1], al[ks][1]);
+        split_bf16(s_H2[k1 * EC + g], s_H2[(k1 + 1) * EC + g], af[ks][2], al[ks][2]);
+        split_bf16(s_H2[k1 * EC + g + 8], s_H2[(k1 + 1) * EC + g + 8], af[ks][3], al[ks][3]);
+    }
     const int ntiles = D.W / 8;
-    uint32_t bn[KSN][2];
-    auto loadb = [&](int nt, uint32_t (*b)[2]) {
-        const uint32_t* row = reinterpret_cast<const uint32_t*>(W3T + (size_t)(nt * 8 + g) * H);
+    for (int nb = warp; nb < ntiles; nb += BATCH * CONV_WARPS) {
+        uint4 bv[BATCH][NV];
 #pragma unroll
-        for (int ks = 0; ks < KSN; ++ks) {
-            b[ks][0] = __ldg(row + ks * 8 + tq);
-            b[ks][1] = __ldg(row + ks * 8 + 4 + tq);
-        }
-    };
-    if (warp < ntiles) loadb(warp, bn);
-    for (int nt = warp; nt < ntiles; nt += CONV_WARPS) {
-        uint32_t bc[KSN][2];
+        for (int j = 0; j < BATCH; ++j) {
+            const int nt = nb + j * CONV_WARPS;
+            if (nt < ntiles) {
+                const uint4* row = reinterpret_cast<const uint4*>(W3T + (size_t)(nt * 8 + g) * H);
 #pragma unroll
-        for (int ks = 0; ks < KSN; ++ks) { bc[ks][0] = bn[ks][0]; bc[ks][1] = bn[ks][1]; }
-        if (nt + CONV_WARPS < ntiles) loadb(nt + CONV_WARPS, bn);
-        float c[MT][4];
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt) c[mt][0] = c[mt][1] = c[mt][2] = c[mt][3] = 0.f;
-#pragma unroll
-        for (int ks = 0; ks < KSN; ++ks)
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt) {
-                mma_bf16(c[mt], af[mt][ks], bc[ks]);
-                if constexpr (SPLIT_ACT) mma_bf16(c[mt], al[mt][ks], bc[ks]);
+                for (int v = 0; v < NV; ++v) bv[j][v] = __ldg(row + tq * NV + v);
             }
-        const int col = nt * 8 + 2 * tq;
+        }
 #pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-            const int r = mt * 16 + g;
-            *reinterpret_cast<float2*>(s_w + r * D.Wpad + col) = make_float2(c[mt][0], c[mt][1]);
-            *reinterpret_cast<float2*>(s_w + (r + 8) * D.Wpad + col) = make_float2(c[mt][2], c[mt][3]);
+        for (int j = 0; j < BATCH; ++j) {
+            const int nt = nb + j * CONV_WARPS;
+            if (nt >= ntiles) break;
+            const uint32_t* bw = reinterpret_cast<const uint32_t*>(bv[j]);
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int ks = 0; ks < KSN; ++ks) {
+                const uint32_t b[2] = {bw[2 * ks], bw[2 * ks + 1]};
+                mma_bf16(c, af[ks], b);
+                if constexpr (SPLIT_ACT) mma_bf16(c, al[ks], b);
+            }
+            const int col = nt * 8 + 2 * tq;
+            *reinterpret_cast<float2*>(s_w + g * D.Wpad + col) = make_float2(c[0], c[1]);
+            *reinterpret_cast<float2*>(s_w + (g + 8) * D.Wpad + col) = make_float2(c[2], c[3]);
         }
     }
     __syncthreads();
 }
 
 // Phase F (BF16): gH2[k][e] = sum_c gw[e][c] W3[k][c]; B operand W3 [H][W] (bf16).
-// The K (column) range is split over the warps, so each dE/dw fragment is read
-// and split once; partial sums meet in shared memory.
+// K (the W columns) runs in blocks of 32 columns split over the warps; each
+// block's A fragment is read and split once, its B fragments come as one 16-byte
+// load per lane and n tile; partial sums meet in shared memory.
 template <int H>
 __device__ __forceinline__ void chunk_gw_gemm_bf16(const ConvDesc& D, const ConvSmem& L, float* smem,
                                                    const __nv_bfloat16* __restrict__ W3h) {
@@ -227,23 +231,29 @@ __device__ __forceinline__ void chunk_gw_gemm_bf16(const ConvDesc& D, const Conv
     float c[NT][4];
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
-    for (int ks = warp; ks < W / 16; ks += CONV_WARPS) {
-        const int c0 = ks * 16 + 2 * tq;
-        const float2 x0 = *reinterpret_cast<const float2*>(s_w + g * D.Wpad + c0);
-        const float2 x1 = *reinterpret_cast<const float2*>(s_w + (g + 8) * D.Wpad + c0);
-        const float2 x2 = *reinterpret_cast<const float2*>(s_w + g * D.Wpad + c0 + 8);
-        const float2 x3 = *reinterpret_cast<const float2*>(s_w + (g + 8) * D.Wpad + c0 + 8);
-        uint32_t a[4], al[4];
-        split_bf16(x0.x, x0.y, a[0], al[0]);
-        split_bf16(x1.x, x1.y, a[1], al[1]);
-        split_bf16(x2.x, x2.y, a[2], al[2]);
-        split_bf16(x3.x, x3.y, a[3], al[3]);
+    for (int kb = warp; kb < W / 32; kb += CONV_WARPS) {
+        uint4 bv[NT];
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            const uint32_t* brow = reinterpret_cast<const uint32_t*>(W3h + (size_t)(nt * 8 + g) * W);
-            const uint32_t b[2] = {__ldg(brow + (c0 >> 1)), __ldg(brow + ((c0 + 8) >> 1))};
-            mma_bf16(c[nt], a, b);
-            if constexpr (SPLIT_ACT) mma_bf16(c[nt], al, b);
+        for (int nt = 0; nt < NT; ++nt)
+            bv[nt] = __ldg(reinterpret_cast<const uint4*>(W3h + (size_t)(nt * 8 + g) * W + kb * 32) + tq);
+        // k step ks covers words kb*16 + 4 tq + 2 ks (+1): columns 32 kb + 8 tq + 4 ks .. + 3
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const int c0 = kb * 32 + 8 * tq + 4 * ks;
+            const float4 r0 = *reinterpret_cast<const float4*>(s_w + g * D.Wpad + c0);
+            const float4 r1 = *reinterpret_cast<const float4*>(s_w + (g + 8) * D.Wpad + c0);
+            uint32_t a[4], al[4];
+            split_bf16(r0.x, r0.y, a[0], al[0]);
+            split_bf16(r1.x, r1.y, a[1], al[1]);
+            split_bf16(r0.z, r0.w, a[2], al[2]);
+            split_bf16(r1.z, r1.w, a[3], al[3]);
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const uint32_t* bw = reinterpret_cast<const uint32_t*>(&bv[nt]);
+                const uint32_t b[2] = {bw[2 * ks], bw[2 * ks + 1]};
+                mma_bf16(c[nt], a, b);
+                if constexpr (SPLIT_ACT) mma_bf16(c[nt], al, b);
+            }
         }
     }
 #pragma unroll
@@ -265,31 +275,56 @@ template <int H>
 __device__ __forceinline__ void hidden_mma(const float* __restrict__ s_in, const __nv_bfloat16* __restrict__ Bn,
                                            float (&c)[4], int nt) {
     constexpr int KSN = H / 16;
+    constexpr int NV = KSN / 2;
     const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
     c[0] = c[1] = c[2] = c[3] = 0.f;
-    const uint32_t* brow = reinterpret_cast<const uint32_t*>(Bn + (size_t)(nt * 8 + g) * H);
+    const uint4* hi = reinterpret_cast<const uint4*>(Bn + (size_t)(nt * 8 + g) * H) + tq * NV;
+    const uint4* lo = reinterpret_cast<const uint4*>(Bn + (size_t)H * H + (size_t)(nt * 8 + g) * H) + tq * NV;
+    uint4 bh[NV], bl[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        bh[v] = __ldg(hi + v);
+        bl[v] = __ldg(lo + v);
+    }
+    const uint32_t* wh = reinterpret_cast<const uint32_t*>(bh);
+    const uint32_t* wl = reinterpret_cast<const uint32_t*>(bl);
 #pragma unroll
     for (int ks = 0; ks < KSN; ++ks) {
-        const int k0 = ks * 16 + 2 * tq;
+        const int k0 = 2 * (tq * 2 * KSN + 2 * ks), k1 = k0 + 2;
         uint32_t a[4], al[4];
         split_bf16(s_in[k0 * EC + g], s_in[(k0 + 1) * EC + g], a[0], al[0]);
         split_bf16(s_in[k0 * EC + g + 8], s_in[(k0 + 1) * EC + g + 8], a[1], al[1]);
-        split_bf16(s_in[(k0 + 8) * EC + g], s_in[(k0 + 9) * EC + g], a[2], al[2]);
-        split_bf16(s_in[(k0 + 8) * EC + g + 8], s_in[(k0 + 9) * EC + g + 8], a[3], al[3]);
-        const uint32_t b[2] = {__ldg(brow + (k0 >> 1)), __ldg(brow + ((k0 + 8) >> 1))};
-        const uint32_t bl[2] = {__ldg(brow + H * H / 2 + (k0 >> 1)), __ldg(brow + H * H / 2 + ((k0 + 8) >> 1))};
+        split_bf16(s_in[k1 * EC + g], s_in[(k1 + 1) * EC + g], a[2], al[2]);
+        split_bf16(s_in[k1 * EC + g + 8], s_in[(k1 + 1) * EC + g + 8], a[3], al[3]);
+        const uint32_t b[2] = {wh[2 * ks], wh[2 * ks + 1]};
+        const uint32_t b2[2] = {wl[2 * ks], wl[2 * ks + 1]};
         mma_bf16(c, a, b);
         if constexpr (SPLIT_ACT) mma_bf16(c, al, b);
-        mma_bf16(c, a, bl);
+        mma_bf16(c, a, b2);
     }
 }
 
 // Phases A-C shared by both kernels.  Leaves s_src/s_dst/Y/B/A1/A2/H2/G filled.
+// Edge data of one chunk, fetched one chunk ahead by threads 0..EC-1.
+struct EdgePrefetch {
+    int src = 0, dst = -1, first = 0;           // first: index of the receiver's first edge
+    float4 geom = make_float4(0.f, 0.f, 0.f, 1.f);
+    __device__ __forceinline__ void fetch(int c0, int E1, const int* __restrict__ dsts,
+                                          const int* __restrict__ srcs, const float4* __restrict__ geoms,
+                                          const int* __restrict__ row_ptr) {
+        const int ge = c0 + (int)threadIdx.x;
+        if ((int)threadIdx.x < EC && ge < E1) {
+            src = srcs[ge];
+            dst = dsts[ge];
+            geom = geoms[ge];
+            first = __ldg(row_ptr + dst);
+        }
+    }
+};
+
 template <int H, bool BF>
 __device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem& L, float* smem,
-                                               int c0, int ne, const int* __restrict__ dst,
-                                               const int* __restrict__ src,
-                                               const float4* __restrict__ geom,
+                                               int c0, int ne, const EdgePrefetch& pf,
                                                const float* __restrict__ W1,
                                                const float* __restrict__ W2,
                                                const __nv_bfloat16* __restrict__ W2T_h) {
@@ -300,10 +335,10 @@ __device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem
     float* s_B = smem + L.B;       // [NB][EC]
     if (t < EC) {
         if (t < ne) {
-            const int ge = c0 + t;
-            s_src[t] = src[ge];
-            s_dst[t] = dst[ge];
-            edge_features(D, geom[ge], s_Y + t * 9, s_B + t, EC);
+            s_src[t] = pf.src;
+            s_dst[t] = pf.dst;
+            reinterpret_cast<int*>(smem + L.first)[t] = pf.first >= c0;   // receiver starts here
+            edge_features(D, pf.geom, s_Y + t * 9, s_B + t, EC);
         } else {
             s_src[t] = 0;
             s_dst[t] = -1;

@@ -5,40 +5,56 @@
 
 namespace sn {
 
-template <int L1, int L2, int L3>
-__device__ __forceinline__ void tp_fwd_group(const PathDesc& P, int u, int c0, int ne,
+// One group = one path and CPL channels per lane (32*CPL channels per warp).
+// The lane walks the chunk's edges, keeps the running message of the current
+// receiver in registers and writes it once when the receiver changes.  The
+// edge's G matrix and the address arithmetic serve all CPL channels.
+template <int L1, int L2, int L3, int CPL>
+__device__ __forceinline__ void tp_fwd_group(const PathDesc& P, int u0, int ne,
                                              const float* s_w, int Wpad, const float* s_G, int nG,
-                                             const int* s_src, const int* s_dst,
-                                             const int* __restrict__ row_ptr,
+                                             const int* s_src, const int* s_dst, const int* s_first,
                                              const float* __restrict__ x, int x_dim,
                                              float* __restrict__ m, int m_dim) {
     constexpr int N1 = 2 * L1 + 1, N3 = 2 * L3 + 1;
-    const int col = P.col0 + u;
-    const float* xb = x + P.x_off + u;
-    float* mb = m + P.m_off + P.m_ch0 + u;
-    float acc[N3];
+    constexpr int PF = (CPL * N1 <= 1) ? 16 : (CPL * N1 <= 2) ? 8 : (CPL * N1 <= 4) ? 4 : 2;   // gathers in flight
+    const int col = P.col0 + u0;
+    const int mul = P.mul;
+    const float* xb = x + P.x_off + u0;
+    float* mb = m + P.m_off + P.m_ch0 + u0;
+    // A receiver that started in this CTA's previous chunk was written there by
+    // this same thread; its partial sum seeds the accumulator, and the load
+    // overlaps the first gathers.
+    float acc[CPL][N3];
+    if (!s_first[0]) {
+        const float* mp = mb + (size_t)s_dst[0] * m_dim;
 #pragma unroll
-    for (int c = 0; c < N3; ++c) acc[c] = 0.0f;
-    int cur = -1;
+        for (int k = 0; k < CPL; ++k)
+#pragma unroll
+            for (int c = 0; c < N3; ++c) acc[k][c] = mp[c * P.m_mul + 32 * k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < CPL; ++k)
+#pragma unroll
+            for (int c = 0; c < N3; ++c) acc[k][c] = 0.0f;
+    }
+    int cur = s_dst[0];
     auto flush = [&](int v) {
         float* mp = mb + (size_t)v * m_dim;
-        if (__ldg(row_ptr + v) >= c0) {
 #pragma unroll
-            for (int c = 0; c < N3; ++c) mp[c * P.m_mul] = acc[c];
-        } else {
+        for (int k = 0; k < CPL; ++k)
 #pragma unroll
-            for (int c = 0; c < N3; ++c) mp[c * P.m_mul] += acc[c];
-        }
+            for (int c = 0; c < N3; ++c) mp[c * P.m_mul + 32 * k] = acc[k][c];
     };
-    constexpr int PF = 4;       // edges whose gathers are in flight together
     for (int e0 = 0; e0 < ne; e0 += PF) {
-        float xv[PF][N1];
+        float xv[PF][CPL][N1];
 #pragma unroll
         for (int q = 0; q < PF; ++q) {
             const int e = min(e0 + q, ne - 1);
             const float* xr = xb + (size_t)s_src[e] * x_dim;
 #pragma unroll
-            for (int a = 0; a < N1; ++a) xv[q][a] = __ldg(xr + a * P.mul);
+            for (int k = 0; k < CPL; ++k)
+#pragma unroll
+                for (int a = 0; a < N1; ++a) xv[q][k][a] = __ldg(xr + a * mul + 32 * k);
         }
 #pragma unroll
         for (int q = 0; q < PF; ++q) {
@@ -46,24 +62,30 @@ __device__ __forceinline__ void tp_fwd_group(const PathDesc& P, int u, int c0, i
             if (e >= ne) break;
             const int v = s_dst[e];
             if (v != cur) {
-                if (cur >= 0) flush(cur);
+                flush(cur);
                 cur = v;
 #pragma unroll
-                for (int c = 0; c < N3; ++c) acc[c] = 0.0f;
+                for (int k = 0; k < CPL; ++k)
+#pragma unroll
+                    for (int c = 0; c < N3; ++c) acc[k][c] = 0.0f;
             }
-            const float wv = s_w[e * Wpad + col];
             float G[((N1 * N3 + 3) / 4) * 4];
             load_G<N1 * N3>(s_G + e * nG + P.g_off, G);
+            const float* wr = s_w + e * Wpad + col;
 #pragma unroll
-            for (int c = 0; c < N3; ++c) {
-                float tt = 0.0f;
+            for (int k = 0; k < CPL; ++k) {
+                const float wv = wr[32 * k];
 #pragma unroll
-                for (int a = 0; a < N1; ++a) tt = fmaf(xv[q][a], G[a * N3 + c], tt);
-                acc[c] = fmaf(wv, tt, acc[c]);
+                for (int c = 0; c < N3; ++c) {
+                    float tt = 0.0f;
+#pragma unroll
+                    for (int a = 0; a < N1; ++a) tt = fmaf(xv[q][k][a], G[a * N3 + c], tt);
+                    acc[k][c] = fmaf(wv, tt, acc[k][c]);
+                }
             }
         }
     }
-    if (cur >= 0) flush(cur);
+    if (ne > 0) flush(cur);
 }
 
 template <int H, bool BF>
@@ -90,24 +112,35 @@ conv_fwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
     const int E0 = row_ptr[v0], E1 = row_ptr[v1];
     const int* s_src = reinterpret_cast<const int*>(smem + L.src);
     const int* s_dst = reinterpret_cast<const int*>(smem + L.dst);
+    const int* s_first = reinterpret_cast<const int*>(smem + L.first);
+    EdgePrefetch pf;
+    pf.fetch(E0, E1, dst, src, geom, row_ptr);
     for (int c0 = E0; c0 < E1; c0 += EC) {
         const int ne = min(EC, E1 - c0);
         __syncthreads();
-        chunk_prologue<H, BF>(D, L, smem, c0, ne, dst, src, geom, W1, W2, W2T_h);
+        chunk_prologue<H, BF>(D, L, smem, c0, ne, pf, W1, W2, W2T_h);
+        pf.fetch(c0 + EC, E1, dst, src, geom, row_ptr);   // next chunk's edges, in flight meanwhile
         if constexpr (BF) chunk_w_gemm_bf16<H>(D, L, smem, W3T_h);
         else chunk_w_gemm_f32<H>(D, L, smem, W3);
         for (int s = 0; s < D.n_slots[warp]; ++s) {
             const int g = D.slot_group[warp][s];
             const PathDesc& P = D.paths[g >> 8];
-            const int u = (g & 255) * 32 + lane;
-            switch (P.kind) {
-#define SN_F(a, b, c) case coupling_kind(a, b, c):                                              \
-                tp_fwd_group<a, b, c>(P, u, c0, ne, smem + L.w, D.Wpad, smem + L.G, D.nG, s_src, \
-                                      s_dst, row_ptr, x, D.x_dim, m, D.m_dim); break;
+            const int lc = g & 3;                      // log2 of channels per lane
+            const int u0 = ((g >> 2) & 63) * (32 << lc) + lane;
+            switch (P.kind * 3 + lc) {
+#define SN_F1(a, b, c, l)                                                                          \
+                case coupling_kind(a, b, c) * 3 + l:                                               \
+                    if constexpr (fwd_cpl_compiled(H, a, 1 << l))                                  \
+                        tp_fwd_group<a, b, c, (1 << l)>(P, u0, ne, smem + L.w, D.Wpad, smem + L.G, \
+                                                        D.nG, s_src, s_dst, s_first, x, D.x_dim, m, \
+                                                        D.m_dim);                                  \
+                    break;
+#define SN_F(a, b, c) SN_F1(a, b, c, 0) SN_F1(a, b, c, 1) SN_F1(a, b, c, 2)
                 SN_F(0, 0, 0) SN_F(0, 1, 1) SN_F(0, 2, 2)
                 SN_F(1, 0, 1) SN_F(1, 1, 0) SN_F(1, 1, 1) SN_F(1, 1, 2) SN_F(1, 2, 1) SN_F(1, 2, 2)
                 SN_F(2, 0, 2) SN_F(2, 1, 1) SN_F(2, 1, 2) SN_F(2, 2, 0) SN_F(2, 2, 1) SN_F(2, 2, 2)
 #undef SN_F
+#undef SN_F1
                 default: break;
             }
         }

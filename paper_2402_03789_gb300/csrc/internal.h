@@ -71,6 +71,14 @@ __host__ __device__ constexpr int coupling_kind(int l1, int l2, int l3) {
     return -1;
 }
 
+// Forward convolution: channels per lane (CPL) that the kernel is compiled for.
+// Several channels per lane share one G matrix and the address arithmetic; the
+// register budget of 2 CTAs per SM allows CPL * (2 l1 + 1) <= 6, and only the
+// H = 64 kernel carries the wider groups.
+__host__ __device__ constexpr bool fwd_cpl_compiled(int H, int l1, int cpl) {
+    return cpl == 1 || (H == 64 && cpl * (2 * l1 + 1) <= 6);
+}
+
 // Path set of a block, known at compile time from (l1, lmax, kind): the
 // couplings (l1, l2, l3) with |l1-l2| <= l3 <= min(l1+l2, lmax), l2 <= lmax;
 // the first block has l1 = 0 only, the last keeps l3 = 0 only.  Same order as
