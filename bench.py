@@ -174,14 +174,15 @@ def oracle_sample(steps=None, seconds=12.0):
                        f"5-layer model) by the FP64 CPU oracle"), (s, spec, w, res)
 
 
-def traffic_for(kernel, source):
-    """DRAM bytes per launch from a committed ncu capture, if taken on this source."""
+def traffic_for(kernel):
+    """DRAM bytes per launch from a committed ncu capture, if it was taken on the current source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        data = json.load(open(path))
-        sha = hashlib.sha256(open(source, "rb").read()).hexdigest()[:16]
-        ent = data.get(kernel)
-        if ent and ent.get("source_sha") == sha:
+        ent = json.load(open(path)).get(kernel)
+        h = hashlib.sha256()
+        for f in ent["source_files"]:
+            h.update(open(os.path.join(ROOT, "paper_2402_03789_gb300", "csrc", f), "rb").read())
+        if h.hexdigest()[:16] == ent["source_sha"]:
             return ent["bytes_per_launch_full_workload"]
     except Exception:
         pass
@@ -344,7 +345,7 @@ def main():
     achieved = alu_step * args.steps / (tot_ms / 1e3) / 1e12
     peak = fp32_alu_peak_tflops(n_sm, 2070.0)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic_for(fam, os.path.join(ROOT, "paper_2402_03789_gb300", "csrc", "conv.cu")),
+                "traffic": traffic_for(fam) if args.workload == WORKLOAD and tc else None,
                 "kernel": fam, "share_of_step": tot_ms / dev_ms,
                 "peak_source": f"FP32 FFMA: {n_sm} SMs x 128 lanes x 2 FLOP x 2070 MHz (unit counts and max clock)",
                 "alu_flops_per_step": alu_step}
