@@ -227,42 +227,72 @@ static sevennet_status upload_linear(sevennet_model* M, const double* w, int row
     return SEVENNET_OK;
 }
 
-// Forward work groups: one path and CPL in {1, 2, 4} channels per lane (the
-// largest CPL that still leaves at least 1.5 groups per warp), assigned to
-// warps longest first.  Encoding: (path << 8) | (channel block << 2) | log2 CPL.
+// Forward work slots: one path set of input irrep l1 (fwd_path_sets) and a block
+// of 32 * CPL channels.  CPL is chosen per set among the compiled widths by
+// trying every combination and keeping the one whose longest-first assignment
+// to the warps has the smallest maximum load (a slot's load: its multiply-adds
+// per edge plus the per-edge gathers and shared-memory loads).  Encoding:
+// (l1 << 11) | (set << 8) | (channel block << 2) | log2 CPL.
 static bool assign_slots(ConvDesc& D, int H) {
-    struct G { int p, ub, lc, cost; };
-    auto groups_for = [&](int cap, std::vector<G>* out) {
-        int n = 0;
-        for (int p = 0; p < D.n_paths; ++p) {
-            const PathDesc& P = D.paths[p];
-            int cpl = std::min(cap, P.mul / 32), lc = 0;
-            while ((1 << (lc + 1)) <= cpl && fwd_cpl_compiled(H, P.l1, 1 << (lc + 1))) ++lc;
-            cpl = 1 << lc;
-            const int n1 = 2 * P.l1 + 1, n3 = 2 * P.l3 + 1;
-            for (int ub = 0; ub < P.mul / (32 * cpl); ++ub, ++n)
-                if (out) out->push_back({p, ub, lc, cpl * (n1 * n3 + n3 + n1) + 4});
+    struct Set { int l1, j, mul, cost, nacc, nG, np; std::vector<int> lcs; };
+    std::vector<Set> sets;
+    for (int l1 = 0; l1 <= D.lmax; ++l1) {
+        if (D.pend[l1] <= D.pbeg[l1]) continue;
+        const PathSets S = fwd_path_sets(l1, D.lmax, D.kind);
+        const PathList pl = path_list(l1, D.lmax, D.kind);
+        for (int j = 0; j < S.n; ++j) {
+            Set st{l1, j, D.mul_in[l1], fwd_set_cost(l1, D.lmax, D.kind, j), fwd_set_nacc(l1, D.lmax, D.kind, j), 0,
+                   S.b[j + 1] - S.b[j], {}};
+            for (int i = S.b[j]; i < S.b[j + 1]; ++i) st.nG += ((2 * l1 + 1) * (2 * pl.l3[i] + 1) + 3) / 4;
+            for (int lc = 0; lc < 3; ++lc)
+                if (fwd_cpl_compiled(H, l1, st.nacc, 1 << lc) && st.mul % (32 << lc) == 0) st.lcs.push_back(lc);
+            if (st.lcs.empty() || st.mul % 32 != 0) return false;
+            sets.push_back(st);
         }
-        return n;
+    }
+    struct Slot { int code, load; };
+    auto build = [&](const std::vector<int>& choice, std::vector<Slot>& out) {
+        out.clear();
+        for (size_t k = 0; k < sets.size(); ++k) {
+            const Set& st = sets[k];
+            const int lc = st.lcs[choice[k]], cpl = 1 << lc;
+            // per edge: multiply-adds, gathers, G quads, weights, edge bookkeeping
+            const int load = cpl * st.cost + cpl * (2 * st.l1 + 1) + st.nG + cpl * st.np + 6;
+            for (int ub = 0; ub < st.mul / (32 * cpl); ++ub)
+                out.push_back({(st.l1 << 11) | (st.j << 8) | (ub << 2) | lc, load});
+        }
     };
-    int cap = 1;
-    for (int c : {4, 2}) {
-        if (groups_for(c, nullptr) * 2 >= 3 * CONV_WARPS) { cap = c; break; }
+    auto lpt = [&](std::vector<Slot> sl, int16_t (*grp)[MAX_SLOTS], int16_t* n) {
+        std::stable_sort(sl.begin(), sl.end(), [](const Slot& a, const Slot& b) { return a.load > b.load; });
+        int load[CONV_WARPS] = {0}, cnt[CONV_WARPS] = {0};
+        for (const Slot& x : sl) {
+            int best = -1;
+            for (int w = 0; w < CONV_WARPS; ++w)
+                if (cnt[w] < MAX_SLOTS && (best < 0 || load[w] < load[best])) best = w;
+            if (best < 0) return -1;
+            if (grp) grp[best][cnt[best]] = (int16_t)x.code;
+            ++cnt[best];
+            load[best] += x.load;
+        }
+        if (n) for (int w = 0; w < CONV_WARPS; ++w) n[w] = (int16_t)cnt[w];
+        int mx = 0;
+        for (int w = 0; w < CONV_WARPS; ++w) mx = std::max(mx, load[w]);
+        return mx;
+    };
+    std::vector<int> choice(sets.size(), 0), best_choice;
+    int best = -1;
+    std::vector<Slot> sl;
+    for (;;) {
+        build(choice, sl);
+        const int mk = lpt(sl, nullptr, nullptr);
+        if (mk >= 0 && (best < 0 || mk < best)) { best = mk; best_choice = choice; }
+        size_t k = 0;
+        while (k < sets.size() && ++choice[k] == (int)sets[k].lcs.size()) choice[k++] = 0;
+        if (k == sets.size()) break;
     }
-    std::vector<G> gs;
-    groups_for(cap, &gs);
-    std::stable_sort(gs.begin(), gs.end(), [](const G& a, const G& b) { return a.cost > b.cost; });
-    int load[CONV_WARPS] = {0};
-    for (int w = 0; w < CONV_WARPS; ++w) D.n_slots[w] = 0;
-    for (const G& g : gs) {
-        int best = -1;
-        for (int w = 0; w < CONV_WARPS; ++w)
-            if (D.n_slots[w] < MAX_SLOTS && (best < 0 || load[w] < load[best])) best = w;
-        if (best < 0 || g.ub > 63) return false;
-        D.slot_group[best][D.n_slots[best]++] = (int16_t)((g.p << 8) | (g.ub << 2) | g.lc);
-        load[best] += g.cost;
-    }
-    return true;
+    if (best < 0) return false;
+    build(best_choice, sl);
+    return lpt(sl, D.slot_group, D.n_slots) >= 0;
 }
 
 }  // namespace sn
@@ -616,7 +646,6 @@ sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const do
         D.env_b = (float)(p * (p + 2.0));
         D.env_c = (float)(p * (p + 1.0) / 2.0);
         D.poly_p = cfg->poly_p;
-        // the H = 32 kernels take one channel per lane
         if (!assign_slots(D, H)) { set_error("block %d: too many channel groups", t); return fail(SEVENNET_EINVAL); }
         // weights
         const std::string pre = "L" + std::to_string(t) + ".";

@@ -3,8 +3,6 @@
 // radial MLP and the edge embedding.  Shared phases live in conv_common.cuh.
 #include "conv_common.cuh"
 
-#include <utility>
-
 namespace sn {
 
 // ------------------------------------------------------------- adjoint
@@ -43,22 +41,6 @@ __device__ __forceinline__ void tp_bwd_path(const PathDesc& P, int u0, int e, in
         CG<L1, L2, L3>::gY(wx, g[k], gY + L2 * L2);
     }
 }
-
-template <typename F, int... Is>
-__device__ __forceinline__ void static_for_impl(F& f, std::integer_sequence<int, Is...>) {
-    (f(std::integral_constant<int, Is>{}), ...);
-}
-
-template <int N, typename F>
-__device__ __forceinline__ void static_for(F&& f) {
-    static_for_impl(f, std::make_integer_sequence<int, N>{});
-}
-
-template <int L1, int LMAX, int KIND>
-struct BlockPaths {
-    static constexpr PathList list = path_list(L1, LMAX, KIND);
-    static constexpr int begin = path_begin(L1, LMAX, KIND);
-};
 
 // All paths of one input irrep l1 for one edge, CPL channels per lane: the
 // channel loads, the path descriptors and the CG code resolve at compile time.

@@ -27,6 +27,8 @@
 #include "internal.h"
 #include "cg_tables.cuh"
 
+#include <utility>
+
 namespace sn {
 
 constexpr int KS = 8;         // k-slice of the W3 staging in phase D
@@ -127,6 +129,23 @@ __device__ __forceinline__ void path_G(int kind, const float* Y, float* g) {
         default: break;
     }
 }
+
+// Compile-time loop and the compile-time path list of one input irrep.
+template <typename F, int... Is>
+__device__ __forceinline__ void static_for_impl(F& f, std::integer_sequence<int, Is...>) {
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+template <int L1, int LMAX, int KIND>
+struct BlockPaths {
+    static constexpr PathList list = path_list(L1, LMAX, KIND);
+    static constexpr int begin = path_begin(L1, LMAX, KIND);
+};
 
 // ---- BF16 tensor-core variants of phases D and F (mma.sync m16n8k16, FP32 accumulate)
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {

@@ -5,45 +5,74 @@
 
 namespace sn {
 
-// One group = one path and CPL channels per lane (32*CPL channels per warp).
-// The lane walks the chunk's edges, keeps the running message of the current
-// receiver in registers and writes it once when the receiver changes.  The
-// edge's G matrix and the address arithmetic serve all CPL channels.
-template <int L1, int L2, int L3, int CPL>
-__device__ __forceinline__ void tp_fwd_group(const PathDesc& P, int u0, int ne,
-                                             const float* s_w, int Wpad, const float* s_G, int nG,
-                                             const int* s_src, const int* s_dst, const int* s_first,
-                                             const float* __restrict__ x, int x_dim,
-                                             float* __restrict__ m, int m_dim) {
-    constexpr int N1 = 2 * L1 + 1, N3 = 2 * L3 + 1;
-    constexpr int PF = (CPL * N1 <= 1) ? 16 : (CPL * N1 <= 2) ? 8 : (CPL * N1 <= 4) ? 4 : 2;   // gathers in flight
-    const int col = P.col0 + u0;
-    const int mul = P.mul;
-    const float* xb = x + P.x_off + u0;
-    float* mb = m + P.m_off + P.m_ch0 + u0;
-    // A receiver that started in this CTA's previous chunk was written there by
-    // this same thread; its partial sum seeds the accumulator, and the load
-    // overlaps the first gathers.
-    float acc[CPL][N3];
+template <int L1, int LMAX, int KIND>
+struct FwdSets {
+    static constexpr PathSets sets = fwd_path_sets(L1, LMAX, KIND);
+};
+
+// Offset of path i of the l1 list inside the running sums of its set.
+template <int L1, int LMAX, int KIND>
+__host__ __device__ constexpr int fwd_acc_off(int j, int i) {
+    const PathList p = path_list(L1, LMAX, KIND);
+    int o = 0;
+    for (int k = fwd_path_sets(L1, LMAX, KIND).b[j]; k < i; ++k) o += 2 * p.l3[k] + 1;
+    return o;
+}
+
+// One work set: the paths [I0, I1) of input irrep L1 for CPL channels per lane
+// (channels u0 + 32 k).  The lane walks the chunk's edges, gathers x_src[L1]
+// once per edge for all paths of the set, keeps the running messages of the
+// current receiver in registers and writes them once when the receiver
+// changes.  A receiver that started in this CTA's previous chunk was written
+// there by this same thread; its partial sums seed the registers, loaded
+// before the first gathers so the two overlap.
+template <int L1, int LMAX, int KIND, int J, int CPL>
+__device__ __forceinline__ void tp_fwd_set(const ConvDesc& D, int u0, int ne, const float* s_w,
+                                           const float* s_G, const int* s_src, const int* s_dst,
+                                           const int* s_first, const float* __restrict__ x,
+                                           float* __restrict__ m) {
+    using BP = BlockPaths<L1, LMAX, KIND>;
+    constexpr int I0 = FwdSets<L1, LMAX, KIND>::sets.b[J];
+    constexpr int I1 = FwdSets<L1, LMAX, KIND>::sets.b[J + 1];
+    constexpr int NP = I1 - I0;
+    constexpr int N1 = 2 * L1 + 1;
+    constexpr int NACC = fwd_set_nacc(L1, LMAX, KIND, J);
+    constexpr int PF = (CPL * N1 <= 2) ? 4 : 2;           // edges whose gathers are in flight together
+    const int mul = D.mul_in[L1];
+    const int Wpad = D.Wpad, nG = D.nG, m_dim = D.m_dim, x_dim = D.x_dim;
+    const float* xb = x + D.x_off[L1] + u0;
+    float acc[CPL][NACC];
+    auto rows = [&](int v, auto&& f) {        // f(path P, acc offset, N3) for every path of the set
+        static_for<NP>([&](auto I) {
+            constexpr int i = I0 + decltype(I)::value;
+            constexpr int N3 = 2 * BP::list.l3[i] + 1;
+            constexpr int off = fwd_acc_off<L1, LMAX, KIND>(J, i);
+            const PathDesc& P = D.paths[BP::begin + i];
+            f(m + (size_t)v * m_dim + P.m_off + P.m_ch0 + u0, P.m_mul, off, std::integral_constant<int, N3>{});
+        });
+    };
     if (!s_first[0]) {
-        const float* mp = mb + (size_t)s_dst[0] * m_dim;
+        rows(s_dst[0], [&](const float* mp, int mm, int off, auto n3) {
 #pragma unroll
-        for (int k = 0; k < CPL; ++k)
+            for (int k = 0; k < CPL; ++k)
 #pragma unroll
-            for (int c = 0; c < N3; ++c) acc[k][c] = mp[c * P.m_mul + 32 * k];
+                for (int c = 0; c < decltype(n3)::value; ++c) acc[k][off + c] = mp[c * mm + 32 * k];
+        });
     } else {
 #pragma unroll
         for (int k = 0; k < CPL; ++k)
 #pragma unroll
-            for (int c = 0; c < N3; ++c) acc[k][c] = 0.0f;
+            for (int c = 0; c < NACC; ++c) acc[k][c] = 0.0f;
     }
     int cur = s_dst[0];
     auto flush = [&](int v) {
-        float* mp = mb + (size_t)v * m_dim;
+        rows(v, [&](const float* mp, int mm, int off, auto n3) {
+            float* mw = const_cast<float*>(mp);
 #pragma unroll
-        for (int k = 0; k < CPL; ++k)
+            for (int k = 0; k < CPL; ++k)
 #pragma unroll
-            for (int c = 0; c < N3; ++c) mp[c * P.m_mul + 32 * k] = acc[k][c];
+                for (int c = 0; c < decltype(n3)::value; ++c) mw[c * mm + 32 * k] = acc[k][off + c];
+        });
     };
     for (int e0 = 0; e0 < ne; e0 += PF) {
         float xv[PF][CPL][N1];
@@ -67,28 +96,64 @@ __device__ __forceinline__ void tp_fwd_group(const PathDesc& P, int u0, int ne,
 #pragma unroll
                 for (int k = 0; k < CPL; ++k)
 #pragma unroll
-                    for (int c = 0; c < N3; ++c) acc[k][c] = 0.0f;
+                    for (int c = 0; c < NACC; ++c) acc[k][c] = 0.0f;
             }
-            float G[((N1 * N3 + 3) / 4) * 4];
-            load_G<N1 * N3>(s_G + e * nG + P.g_off, G);
-            const float* wr = s_w + e * Wpad + col;
+            static_for<NP>([&](auto I) {
+                constexpr int i = I0 + decltype(I)::value;
+                constexpr int N3 = 2 * BP::list.l3[i] + 1;
+                constexpr int off = fwd_acc_off<L1, LMAX, KIND>(J, i);
+                const PathDesc& P = D.paths[BP::begin + i];
+                float G[((N1 * N3 + 3) / 4) * 4];
+                load_G<N1 * N3>(s_G + e * nG + P.g_off, G);
+                const float* wr = s_w + e * Wpad + P.col0 + u0;
 #pragma unroll
-            for (int k = 0; k < CPL; ++k) {
-                const float wv = wr[32 * k];
+                for (int k = 0; k < CPL; ++k) {
+                    const float wv = wr[32 * k];
 #pragma unroll
-                for (int c = 0; c < N3; ++c) {
-                    float tt = 0.0f;
+                    for (int c = 0; c < N3; ++c) {
+                        float tt = 0.0f;
 #pragma unroll
-                    for (int a = 0; a < N1; ++a) tt = fmaf(xv[q][k][a], G[a * N3 + c], tt);
-                    acc[k][c] = fmaf(wv, tt, acc[k][c]);
+                        for (int a = 0; a < N1; ++a) tt = fmaf(xv[q][k][a], G[a * N3 + c], tt);
+                        acc[k][off + c] = fmaf(wv, tt, acc[k][off + c]);
+                    }
                 }
-            }
+            });
         }
     }
     if (ne > 0) flush(cur);
 }
 
-template <int H, bool BF>
+// Phase E of the forward: every warp runs its work sets over the chunk.
+template <int H, int LMAX, int KIND>
+__device__ __forceinline__ void tp_fwd_chunk(const ConvDesc& D, int ne, const float* s_w, const float* s_G,
+                                             const int* s_src, const int* s_dst, const int* s_first,
+                                             const float* __restrict__ x, float* __restrict__ m) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int s = 0; s < D.n_slots[warp]; ++s) {
+        const int g = D.slot_group[warp][s];
+        const int lc = g & 3, ub = (g >> 2) & 63, set = (g >> 8) & 7, l1 = (g >> 11) & 3;
+        const int u0 = ub * (32 << lc) + lane;
+        static_for<LMAX + 1>([&](auto L) {
+            constexpr int L1 = decltype(L)::value;
+            static_for<FWD_MAX_SETS>([&](auto Jc) {
+                constexpr int J = decltype(Jc)::value;
+                if constexpr (J < FwdSets<L1, LMAX, KIND>::sets.n) {
+                    constexpr int NACC = fwd_set_nacc(L1, LMAX, KIND, J);
+                    static_for<3>([&](auto Cc) {
+                        constexpr int LC = decltype(Cc)::value;
+                        if constexpr (fwd_cpl_compiled(H, L1, NACC, 1 << LC)) {
+                            if (l1 == L1 && set == J && lc == LC)
+                                tp_fwd_set<L1, LMAX, KIND, J, (1 << LC)>(D, u0, ne, s_w, s_G, s_src, s_dst,
+                                                                        s_first, x, m);
+                        }
+                    });
+                }
+            });
+        });
+    }
+}
+
+template <int H, bool BF, int LMAX>
 __global__ void __launch_bounds__(CONV_THREADS, 2)
 conv_fwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __restrict__ W2,
                 const float* __restrict__ W3, const __nv_bfloat16* __restrict__ W3T_h,
@@ -122,27 +187,11 @@ conv_fwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
         pf.fetch(c0 + EC, E1, dst, src, geom, row_ptr);   // next chunk's edges, in flight meanwhile
         if constexpr (BF) chunk_w_gemm_bf16<H>(D, L, smem, W3T_h);
         else chunk_w_gemm_f32<H>(D, L, smem, W3);
-        for (int s = 0; s < D.n_slots[warp]; ++s) {
-            const int g = D.slot_group[warp][s];
-            const PathDesc& P = D.paths[g >> 8];
-            const int lc = g & 3;                      // log2 of channels per lane
-            const int u0 = ((g >> 2) & 63) * (32 << lc) + lane;
-            switch (P.kind * 3 + lc) {
-#define SN_F1(a, b, c, l)                                                                          \
-                case coupling_kind(a, b, c) * 3 + l:                                               \
-                    if constexpr (fwd_cpl_compiled(H, a, 1 << l))                                  \
-                        tp_fwd_group<a, b, c, (1 << l)>(P, u0, ne, smem + L.w, D.Wpad, smem + L.G, \
-                                                        D.nG, s_src, s_dst, s_first, x, D.x_dim, m, \
-                                                        D.m_dim);                                  \
-                    break;
-#define SN_F(a, b, c) SN_F1(a, b, c, 0) SN_F1(a, b, c, 1) SN_F1(a, b, c, 2)
-                SN_F(0, 0, 0) SN_F(0, 1, 1) SN_F(0, 2, 2)
-                SN_F(1, 0, 1) SN_F(1, 1, 0) SN_F(1, 1, 1) SN_F(1, 1, 2) SN_F(1, 2, 1) SN_F(1, 2, 2)
-                SN_F(2, 0, 2) SN_F(2, 1, 1) SN_F(2, 1, 2) SN_F(2, 2, 0) SN_F(2, 2, 1) SN_F(2, 2, 2)
-#undef SN_F
-#undef SN_F1
-                default: break;
-            }
+        switch (D.kind) {
+            case 0: tp_fwd_chunk<H, LMAX, 0>(D, ne, smem + L.w, smem + L.G, s_src, s_dst, s_first, x, m); break;
+            case 1: tp_fwd_chunk<H, LMAX, 1>(D, ne, smem + L.w, smem + L.G, s_src, s_dst, s_first, x, m); break;
+            case 2: tp_fwd_chunk<H, LMAX, 2>(D, ne, smem + L.w, smem + L.G, s_src, s_dst, s_first, x, m); break;
+            default: tp_fwd_chunk<H, LMAX, 3>(D, ne, smem + L.w, smem + L.G, s_src, s_dst, s_first, x, m); break;
         }
     }
 }
@@ -171,14 +220,18 @@ void conv_prepare_edges(int64_t n_atoms, int64_t n_edges, const int* row_ptr, co
 size_t conv_smem_bytes(const ConvDesc& D, int H, bool bwd) { return smem_bytes(D, H, bwd); }
 
 sevennet_status conv_configure_fwd(int H, size_t need) {
-    static size_t granted[2][2] = {{0, 0}, {0, 0}};
+    static size_t granted[2] = {0, 0};
     const int hi = H == 64 ? 1 : 0;
     if (H == 64) {
-        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<64, false>, need, &granted[hi][0]));
-        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<64, true>, need, &granted[hi][1]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<64, false, 1>, need, &granted[hi]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<64, true, 1>, need, &granted[hi]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<64, false, 2>, need, &granted[hi]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<64, true, 2>, need, &granted[hi]));
     } else if (H == 32) {
-        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<32, false>, need, &granted[hi][0]));
-        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<32, true>, need, &granted[hi][1]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<32, false, 1>, need, &granted[hi]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<32, true, 1>, need, &granted[hi]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<32, false, 2>, need, &granted[hi]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<32, true, 2>, need, &granted[hi]));
     } else {
         set_error("radial MLP hidden width must be 32 or 64");
         return SEVENNET_EINVAL;
@@ -192,10 +245,16 @@ void launch_conv_fwd(const LayerDev& L, int H, sevennet_precision prec, int64_t 
     const int grid = conv_grid(n_atoms);
     const size_t sm = smem_bytes(L.conv, H, false);
     const bool bf = prec == SEVENNET_BF16;
-#define SN_LF(HH, BB) conv_fwd_kernel<HH, BB><<<grid, CONV_THREADS, sm, st>>>(                     \
+#define SN_LF(HH, BB, LL) conv_fwd_kernel<HH, BB, LL><<<grid, CONV_THREADS, sm, st>>>(             \
         L.conv, L.mlp0, L.mlp1, L.mlp2, L.mlp2h, L.mlp1Th, (int)n_atoms, (int)n_edges, row_ptr, dst, src, geom, x, m)
-    if (H == 64) { if (bf) SN_LF(64, true); else SN_LF(64, false); }
-    else         { if (bf) SN_LF(32, true); else SN_LF(32, false); }
+    const int lm = L.conv.lmax;
+    if (H == 64) {
+        if (bf) { if (lm == 2) SN_LF(64, true, 2); else SN_LF(64, true, 1); }
+        else    { if (lm == 2) SN_LF(64, false, 2); else SN_LF(64, false, 1); }
+    } else {
+        if (bf) { if (lm == 2) SN_LF(32, true, 2); else SN_LF(32, true, 1); }
+        else    { if (lm == 2) SN_LF(32, false, 2); else SN_LF(32, false, 1); }
+    }
 #undef SN_LF
 }
 

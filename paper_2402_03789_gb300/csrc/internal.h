@@ -71,14 +71,6 @@ __host__ __device__ constexpr int coupling_kind(int l1, int l2, int l3) {
     return -1;
 }
 
-// Forward convolution: channels per lane (CPL) that the kernel is compiled for.
-// Several channels per lane share one G matrix and the address arithmetic; the
-// register budget of 2 CTAs per SM allows CPL * (2 l1 + 1) <= 6, and only the
-// H = 64 kernel carries the wider groups.
-__host__ __device__ constexpr bool fwd_cpl_compiled(int H, int l1, int cpl) {
-    return cpl == 1 || (H == 64 && cpl * (2 * l1 + 1) <= 6);
-}
-
 // Path set of a block, known at compile time from (l1, lmax, kind): the
 // couplings (l1, l2, l3) with |l1-l2| <= l3 <= min(l1+l2, lmax), l2 <= lmax;
 // the first block has l1 = 0 only, the last keeps l3 = 0 only.  Same order as
@@ -106,6 +98,64 @@ __host__ __device__ constexpr int path_begin(int l1, int lmax, int kind) {
     int s = 0;
     for (int l = 0; l < l1; ++l) s += path_list(l, lmax, kind).n;
     return s;
+}
+
+// Forward convolution work sets: the path list of one input irrep l1 split into
+// contiguous subsets of at most fwd_set_cap(kind) multiply-adds per channel and
+// edge (a path costs (2 l1 + 1)(2 l3 + 1) for x G and 2 l3 + 1 for the weight).
+// One set shares the gather of x_src[l1] over its paths; its running sums stay
+// in registers.  The first block (scalar input only) uses small sets so that its
+// few paths still give every warp work.
+constexpr int FWD_MAX_SETS = 6;
+__host__ __device__ constexpr int fwd_set_cap(int kind) { return (kind & 1) ? 8 : 48; }
+
+struct PathSets {
+    int n;          // number of sets
+    int b[FWD_MAX_SETS + 1];   // set j holds paths [b[j], b[j + 1]) of path_list(l1, lmax, kind)
+};
+
+__host__ __device__ constexpr int fwd_path_cost(int l1, int l3) { return (2 * l1 + 1) * (2 * l3 + 1) + 2 * l3 + 1; }
+
+__host__ __device__ constexpr PathSets fwd_path_sets(int l1, int lmax, int kind) {
+    PathSets s{0, {0, 0, 0, 0, 0, 0, 0}};
+    const PathList p = path_list(l1, lmax, kind);
+    if (p.n == 0) return s;
+    int cost = 0;
+    for (int i = 0; i < p.n; ++i) {
+        const int c = fwd_path_cost(l1, p.l3[i]);
+        if (cost > 0 && cost + c > fwd_set_cap(kind)) {
+            s.b[++s.n] = i;
+            cost = 0;
+        }
+        cost += c;
+    }
+    s.b[++s.n] = p.n;
+    return s;
+}
+
+// Running sums per channel of set j: sum of 2 l3 + 1 over its paths.
+__host__ __device__ constexpr int fwd_set_nacc(int l1, int lmax, int kind, int j) {
+    const PathList p = path_list(l1, lmax, kind);
+    const PathSets s = fwd_path_sets(l1, lmax, kind);
+    int n = 0;
+    for (int i = s.b[j]; i < s.b[j + 1]; ++i) n += 2 * p.l3[i] + 1;
+    return n;
+}
+
+__host__ __device__ constexpr int fwd_set_cost(int l1, int lmax, int kind, int j) {
+    const PathList p = path_list(l1, lmax, kind);
+    const PathSets s = fwd_path_sets(l1, lmax, kind);
+    int n = 0;
+    for (int i = s.b[j]; i < s.b[j + 1]; ++i) n += fwd_path_cost(l1, p.l3[i]);
+    return n;
+}
+
+// Channels per lane (CPL) the forward kernel is compiled for: several channels
+// share one G matrix and the address arithmetic.  The register budget of 2 CTAs
+// per SM allows CPL (2 l1 + 1) <= 6 gathered values and CPL * nacc <= 20 running
+// sums; only the H = 64 kernel carries the wider groups.
+__host__ __device__ constexpr bool fwd_cpl_compiled(int H, int l1, int nacc, int cpl) {
+    return cpl == 1 || (H == 64 && cpl * (2 * l1 + 1) <= 6 && cpl * nacc <= 20);
 }
 
 struct PathDesc {
@@ -140,7 +190,7 @@ struct ConvDesc {
     int32_t poly_p;
     PathDesc paths[MAX_PATHS];
     int16_t n_slots[CONV_WARPS];
-    int16_t slot_group[CONV_WARPS][MAX_SLOTS];  // (path << 8) | channel block
+    int16_t slot_group[CONV_WARPS][MAX_SLOTS];  // (l1 << 11) | (set << 8) | (channel block << 2) | log2 CPL
 };
 
 // One row-block matrix product of a per-irrep linear: rows are (atom, m)
