@@ -180,7 +180,7 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
             __syncthreads();       // every read of A2 (the silu' above) is done
             if (nt < H / 8) {
                 const int k = nt * 8 + 2 * tq;
-                const int o[4] = {k * EC + g, (k + 1) * EC + g, k * EC + g + 8, (k + 1) * EC + g + 8};
+                const int o[4] = {hk<H>(k, g), hk<H>(k + 1, g), hk<H>(k, g + 8), hk<H>(k + 1, g + 8)};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) s_A2[o[q]] = c[q] * dsiluf_(s_A1[o[q]]);
             }
@@ -193,7 +193,7 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
 #pragma unroll 8
                 for (int j = 0; j < H; ++j) {
                     const float4 b = __ldg(reinterpret_cast<const float4*>(W2T + j * H) + kq);
-                    const float a = s_gH[j * EC + e];
+                    const float a = s_gH[hk<H>(j, e)];
                     a0 = fmaf(a, b.x, a0);
                     a1 = fmaf(a, b.y, a1);
                     a2 = fmaf(a, b.z, a2);
@@ -207,7 +207,7 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
                 const int kq = idx / EC, e = idx % EC;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int o = (4 * kq + q) * EC + e;
+                    const int o = hk<H>(4 * kq + q, e);
                     s_A2[o] = ga[nq][q] * dsiluf_(s_A1[o]);
                 }
             }
@@ -218,7 +218,7 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
             const int n = i / EC, e = i % EC;
             float a = 0.0f;
 #pragma unroll 8
-            for (int k = 0; k < H; ++k) a = fmaf(s_A2[k * EC + e], __ldg(W1 + n * H + k), a);
+            for (int k = 0; k < H; ++k) a = fmaf(s_A2[hk<H>(k, e)], __ldg(W1 + n * H + k), a);
             s_gB[i] = a;
         }
         __syncthreads();

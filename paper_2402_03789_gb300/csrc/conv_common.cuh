@@ -41,6 +41,27 @@ struct ConvSmem {
 
 __host__ __device__ inline int rup4(int x) { return (x + 3) & ~3; }
 
+// Index of element (k, e) of an [H][EC] activation tile (EC = 16).  Rows k and
+// k + 1 share one 32-word line, and the line is XOR-permuted in 8-word steps by
+// t(k) = (4 k / H + k / 2) mod 4.  The MMA fragment loads (the four tq lanes
+// read rows H/4 apart) and the accumulator stores (rows 2 tq, 2 tq + 1) then
+// touch 32 distinct banks, and four consecutive e stay contiguous and aligned.
+template <int H>
+__device__ __forceinline__ int hk(int k, int e) {
+    const int t = ((k * 4 / H) + (k >> 1)) & 3;
+    return ((k >> 1) << 5) | ((((k & 1) << 4) | e) ^ (t << 3));
+}
+
+// Inverse of hk: the (k, e) stored at position i.
+template <int H>
+__device__ __forceinline__ void hk_inv(int i, int& k, int& e) {
+    const int line = i >> 5;
+    const int t = ((line * 8 / H) + line) & 3;         // 4 k / H with k = 2 line (H / 4 is even)
+    const int p = (i & 31) ^ (t << 3);
+    k = 2 * line + (p >> 4);
+    e = p & 15;
+}
+
 __host__ __device__ inline ConvSmem conv_smem_layout(int Wpad, int H, int nG, bool bwd) {
     ConvSmem s;
     int o = 0;
@@ -195,10 +216,10 @@ __device__ __forceinline__ void chunk_w_gemm_bf16(const ConvDesc& D, const ConvS
 #pragma unroll
     for (int ks = 0; ks < KSN; ++ks) {
         const int k0 = 2 * (tq * 2 * KSN + 2 * ks), k1 = k0 + 2;
-        split_bf16(s_H2[k0 * EC + g], s_H2[(k0 + 1) * EC + g], af[ks][0], al[ks][0]);
-        split_bf16(s_H2[k0 * EC + g + 8], s_H2[(k0 + 1) * EC + g + 8], af[ks][1], al[ks][1]);
-        split_bf16(s_H2[k1 * EC + g], s_H2[(k1 + 1) * EC + g], af[ks][2], al[ks][2]);
-        split_bf16(s_H2[k1 * EC + g + 8], s_H2[(k1 + 1) * EC + g + 8], af[ks][3], al[ks][3]);
+        split_bf16(s_H2[hk<H>(k0, g)], s_H2[hk<H>(k0 + 1, g)], af[ks][0], al[ks][0]);
+        split_bf16(s_H2[hk<H>(k0, g + 8)], s_H2[hk<H>(k0 + 1, g + 8)], af[ks][1], al[ks][1]);
+        split_bf16(s_H2[hk<H>(k1, g)], s_H2[hk<H>(k1 + 1, g)], af[ks][2], al[ks][2]);
+        split_bf16(s_H2[hk<H>(k1, g + 8)], s_H2[hk<H>(k1 + 1, g + 8)], af[ks][3], al[ks][3]);
     }
     const int ntiles = D.W / 8;
     for (int nb = warp; nb < ntiles; nb += BATCH * CONV_WARPS) {
@@ -278,10 +299,10 @@ __device__ __forceinline__ void chunk_gw_gemm_bf16(const ConvDesc& D, const Conv
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt) {
         const int k = nt * 8 + 2 * tq;
-        atomicAdd(s_gH + k * EC + g, c[nt][0]);
-        atomicAdd(s_gH + (k + 1) * EC + g, c[nt][1]);
-        atomicAdd(s_gH + k * EC + g + 8, c[nt][2]);
-        atomicAdd(s_gH + (k + 1) * EC + g + 8, c[nt][3]);
+        atomicAdd(s_gH + hk<H>(k, g), c[nt][0]);
+        atomicAdd(s_gH + hk<H>(k + 1, g), c[nt][1]);
+        atomicAdd(s_gH + hk<H>(k, g + 8), c[nt][2]);
+        atomicAdd(s_gH + hk<H>(k + 1, g + 8), c[nt][3]);
     }
     __syncthreads();
 }
@@ -311,10 +332,10 @@ __device__ __forceinline__ void hidden_mma(const float* __restrict__ s_in, const
     for (int ks = 0; ks < KSN; ++ks) {
         const int k0 = 2 * (tq * 2 * KSN + 2 * ks), k1 = k0 + 2;
         uint32_t a[4], al[4];
-        split_bf16(s_in[k0 * EC + g], s_in[(k0 + 1) * EC + g], a[0], al[0]);
-        split_bf16(s_in[k0 * EC + g + 8], s_in[(k0 + 1) * EC + g + 8], a[1], al[1]);
-        split_bf16(s_in[k1 * EC + g], s_in[(k1 + 1) * EC + g], a[2], al[2]);
-        split_bf16(s_in[k1 * EC + g + 8], s_in[(k1 + 1) * EC + g + 8], a[3], al[3]);
+        split_bf16(s_in[hk<H>(k0, g)], s_in[hk<H>(k0 + 1, g)], a[0], al[0]);
+        split_bf16(s_in[hk<H>(k0, g + 8)], s_in[hk<H>(k0 + 1, g + 8)], a[1], al[1]);
+        split_bf16(s_in[hk<H>(k1, g)], s_in[hk<H>(k1 + 1, g)], a[2], al[2]);
+        split_bf16(s_in[hk<H>(k1, g + 8)], s_in[hk<H>(k1 + 1, g + 8)], a[3], al[3]);
         const uint32_t b[2] = {wh[2 * ks], wh[2 * ks + 1]};
         const uint32_t b2[2] = {wl[2 * ks], wl[2 * ks + 1]};
         mma_bf16(c, a, b);
@@ -371,8 +392,9 @@ __device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem
     float* s_A2 = smem + L.A2;
     float* s_H2 = smem + L.H2;
     float* s_H1 = smem + L.stage;
-    for (int i = t; i < H * EC; i += CONV_THREADS) {
-        const int j = i / EC, e = i % EC;
+    for (int i = t; i < H * EC; i += CONV_THREADS) {     // i: storage position of (j, e)
+        int j, e;
+        hk_inv<H>(i, j, e);
         float a = 0.0f;
         for (int n = 0; n < D.n_basis; ++n) a = fmaf(s_B[n * EC + e], __ldg(W1 + n * H + j), a);
         s_A1[i] = a;
@@ -391,7 +413,7 @@ __device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem
             float c[4];
             hidden_mma<H>(s_H1, W2T_h, c, nt);
             const int j = nt * 8 + 2 * tq;
-            const int o[4] = {j * EC + g, (j + 1) * EC + g, j * EC + g + 8, (j + 1) * EC + g + 8};
+            const int o[4] = {hk<H>(j, g), hk<H>(j + 1, g), hk<H>(j, g + 8), hk<H>(j + 1, g + 8)};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 s_A2[o[q]] = c[q];
@@ -406,7 +428,7 @@ __device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem
 #pragma unroll 8
             for (int k = 0; k < H; ++k) {
                 const float4 b = __ldg(reinterpret_cast<const float4*>(W2 + k * H) + jq);
-                const float a = s_H1[k * EC + e];
+                const float a = s_H1[hk<H>(k, e)];
                 a0 = fmaf(a, b.x, a0);
                 a1 = fmaf(a, b.y, a1);
                 a2 = fmaf(a, b.z, a2);
@@ -415,7 +437,7 @@ __device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem
             const float av[4] = {a0, a1, a2, a3};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int o = (4 * jq + q) * EC + e;
+                const int o = hk<H>(4 * jq + q, e);
                 s_A2[o] = av[q];
                 s_H2[o] = siluf_(av[q]);
             }
@@ -457,7 +479,7 @@ __device__ __forceinline__ void chunk_w_gemm_f32(const ConvDesc& D, const ConvSm
             __syncthreads();
 #pragma unroll
             for (int kk = 0; kk < KS; ++kk) {
-                const float4 a = *reinterpret_cast<const float4*>(s_H2 + (k0 + kk) * EC + 4 * eg);
+                const float4 a = *reinterpret_cast<const float4*>(s_H2 + hk<H>(k0 + kk, 4 * eg));
                 const float av[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
                 for (int j = 0; j < NQ; ++j) {
@@ -582,7 +604,7 @@ __device__ __forceinline__ void chunk_gw_gemm_f32(const ConvDesc& D, const ConvS
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int e = eg * EPT + i, k = 4 * kq + q;
-                s_gH[k * EC + e] = acc[i][q] + red[e * H + k];
+                s_gH[hk<H>(k, e)] = acc[i][q] + red[e * H + k];
             }
     }
     __syncthreads();
