@@ -145,13 +145,18 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
     const int* s_dst = reinterpret_cast<const int*>(smem + L.dst);
     float* s_w = smem + L.w;
     float* s_gY = smem + L.gY;
+    load_W1<H>(D, L, smem, W1);
+    float* s_gdp = smem + L.gdp;
     EdgePrefetch pf;
     pf.fetch(E0, E1, dst, src, geom, row_ptr);
     for (int c0 = E0; c0 < E1; c0 += EC) {
         const int ne = min(EC, E1 - c0);
         __syncthreads();
-        chunk_prologue<H, BF>(D, L, smem, c0, ne, pf, W1, W2, W2T_h);
+        chunk_prologue<H, BF>(D, L, smem, c0, ne, pf, W2, W2T_h);
         pf.fetch(c0 + EC, E1, dst, src, geom, row_ptr);   // next chunk's edges, in flight meanwhile
+        // dE/dd of the blocks done so far, copied to shared memory for phase G
+        if (t < 3 * ne) cp_async4(s_gdp + t, gd + (size_t)c0 * 3 + t);
+        cp_async_commit();
         if constexpr (BF) chunk_w_gemm_bf16<H>(D, L, smem, W3T_h);
         else chunk_w_gemm_f32<H>(D, L, smem, W3);
         // E: per-edge adjoint of the tensor product (path lists fixed per block kind);
@@ -176,7 +181,11 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
             const int lane = t & 31, g = lane >> 2, tq = lane & 3;
             float c[4] = {0.f, 0.f, 0.f, 0.f};
             const int nt = warp;
-            if (nt < H / 8) hidden_mma<H>(s_gH, W2_h, c, nt);
+            if (nt < H / 8) {
+                HiddenB<H> hb;
+                hidden_load<H>(W2_h, nt, hb);
+                hidden_mma<H>(s_gH, hb, c);
+            }
             __syncthreads();       // every read of A2 (the silu' above) is done
             if (nt < H / 8) {
                 const int k = nt * 8 + 2 * tq;
@@ -218,13 +227,14 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
             const int n = i / EC, e = i % EC;
             float a = 0.0f;
 #pragma unroll 8
-            for (int k = 0; k < H; ++k) a = fmaf(s_A2[hk<H>(k, e)], __ldg(W1 + n * H + k), a);
+            for (int k = 0; k < H; ++k) a = fmaf(s_A2[hk<H>(k, e)], smem[L.W1 + n * H + k], a);
             s_gB[i] = a;
         }
+        cp_async_wait_all();
         __syncthreads();
         // G: dE/dd = (dE/dr) u + (I - u u^T) dE/du / r
         if (t < ne) {
-            const float4 g = geom[c0 + t];
+            const float4 g = reinterpret_cast<const float4*>(smem + L.geo)[t];
             const float r = g.w, inv = 1.0f / r;
             const float ux = g.x * inv, uy = g.y * inv, uz = g.z * inv;
             float env, denv;
@@ -256,9 +266,9 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
             }
             const float dot = gux * ux + guy * uy + guz * uz;
             float* o = gd + (size_t)(c0 + t) * 3;
-            o[0] += dEdr * ux + (gux - dot * ux) * inv;
-            o[1] += dEdr * uy + (guy - dot * uy) * inv;
-            o[2] += dEdr * uz + (guz - dot * uz) * inv;
+            o[0] = s_gdp[3 * t] + dEdr * ux + (gux - dot * ux) * inv;
+            o[1] = s_gdp[3 * t + 1] + dEdr * uy + (guy - dot * uy) * inv;
+            o[2] = s_gdp[3 * t + 2] + dEdr * uz + (guz - dot * uz) * inv;
         }
     }
 }

@@ -36,7 +36,7 @@ constexpr int DCOLS = 512;    // columns per pass of phase D
 constexpr int CS = 32;        // column slice of phase F (adjoint W3 product)
 
 struct ConvSmem {
-    int w, stage, A1, A2, H2, gH, G, Y, B, gY, src, dst, first, total;
+    int w, stage, A1, A2, H2, gH, G, Y, B, gY, src, dst, first, W1, geo, gdp, total;
 };
 
 __host__ __device__ inline int rup4(int x) { return (x + 3) & ~3; }
@@ -78,6 +78,9 @@ __host__ __device__ inline ConvSmem conv_smem_layout(int Wpad, int H, int nG, bo
     s.src = o;   o += EC;
     s.dst = o;   o += EC;
     s.first = o; o += EC;
+    s.W1 = o;    o += MAX_NB * H;          // radial MLP input layer, loaded once per CTA
+    s.geo = o;   o += 4 * EC;              // (d, r) of the chunk's edges
+    s.gdp = o;   o += bwd ? 3 * EC : 0;    // dE/dd of earlier blocks, prefetched (adjoint)
     s.total = o;
     return s;
 }
@@ -150,6 +153,14 @@ __device__ __forceinline__ void path_G(int kind, const float* Y, float* g) {
         default: break;
     }
 }
+
+// 4-byte asynchronous global -> shared copy (no register staging).
+__device__ __forceinline__ void cp_async4(float* s, const float* g) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Compile-time loop and the compile-time path list of one input irrep.
 template <typename F, int... Is>
@@ -312,22 +323,30 @@ __device__ __forceinline__ void chunk_gw_gemm_bf16(const ConvDesc& D, const Conv
 //   hi + lo BF16 pair; three MMAs per k step (hi*hi, lo*hi, hi*lo).
 // The 16 edges of the chunk are one m tile; warps take n tiles of 8 outputs.
 template <int H>
-__device__ __forceinline__ void hidden_mma(const float* __restrict__ s_in, const __nv_bfloat16* __restrict__ Bn,
-                                           float (&c)[4], int nt) {
-    constexpr int KSN = H / 16;
-    constexpr int NV = KSN / 2;
+struct HiddenB {                                   // B fragments of one n tile, hi and lo
+    uint4 hi[H / 32], lo[H / 32];
+};
+
+template <int H>
+__device__ __forceinline__ void hidden_load(const __nv_bfloat16* __restrict__ Bn, int nt, HiddenB<H>& b) {
+    constexpr int NV = H / 32;
     const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
-    c[0] = c[1] = c[2] = c[3] = 0.f;
     const uint4* hi = reinterpret_cast<const uint4*>(Bn + (size_t)(nt * 8 + g) * H) + tq * NV;
     const uint4* lo = reinterpret_cast<const uint4*>(Bn + (size_t)H * H + (size_t)(nt * 8 + g) * H) + tq * NV;
-    uint4 bh[NV], bl[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        bh[v] = __ldg(hi + v);
-        bl[v] = __ldg(lo + v);
+        b.hi[v] = __ldg(hi + v);
+        b.lo[v] = __ldg(lo + v);
     }
-    const uint32_t* wh = reinterpret_cast<const uint32_t*>(bh);
-    const uint32_t* wl = reinterpret_cast<const uint32_t*>(bl);
+}
+
+template <int H>
+__device__ __forceinline__ void hidden_mma(const float* __restrict__ s_in, const HiddenB<H>& bf, float (&c)[4]) {
+    constexpr int KSN = H / 16;
+    const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+    c[0] = c[1] = c[2] = c[3] = 0.f;
+    const uint32_t* wh = reinterpret_cast<const uint32_t*>(bf.hi);
+    const uint32_t* wl = reinterpret_cast<const uint32_t*>(bf.lo);
 #pragma unroll
     for (int ks = 0; ks < KSN; ++ks) {
         const int k0 = 2 * (tq * 2 * KSN + 2 * ks), k1 = k0 + 2;
@@ -362,13 +381,20 @@ struct EdgePrefetch {
     }
 };
 
+// Radial MLP input layer into shared memory (once per CTA; the first chunk's
+// barrier publishes it).
+template <int H>
+__device__ __forceinline__ void load_W1(const ConvDesc& D, const ConvSmem& L, float* smem,
+                                        const float* __restrict__ W1) {
+    for (int i = threadIdx.x; i < D.n_basis * H; i += CONV_THREADS) smem[L.W1 + i] = W1[i];
+}
+
 template <int H, bool BF>
 __device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem& L, float* smem,
                                                int c0, int ne, const EdgePrefetch& pf,
-                                               const float* __restrict__ W1,
                                                const float* __restrict__ W2,
                                                const __nv_bfloat16* __restrict__ W2T_h) {
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, warp = t >> 5;
     int* s_src = reinterpret_cast<int*>(smem + L.src);
     int* s_dst = reinterpret_cast<int*>(smem + L.dst);
     float* s_Y = smem + L.Y;
@@ -378,27 +404,43 @@ __device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem
             s_src[t] = pf.src;
             s_dst[t] = pf.dst;
             reinterpret_cast<int*>(smem + L.first)[t] = pf.first >= c0;   // receiver starts here
+            reinterpret_cast<float4*>(smem + L.geo)[t] = pf.geom;
             edge_features(D, pf.geom, s_Y + t * 9, s_B + t, EC);
         } else {
             s_src[t] = 0;
             s_dst[t] = -1;
+            reinterpret_cast<float4*>(smem + L.geo)[t] = make_float4(0.f, 0.f, 0.f, 1.f);
             for (int i = 0; i < 9; ++i) s_Y[t * 9 + i] = 0.0f;
             for (int n = 0; n < D.n_basis; ++n) s_B[n * EC + t] = 0.0f;
         }
     }
     __syncthreads();
-    // B: A1 = B @ W1 (layout [H][EC]); H1 = silu(A1) lives in the staging area until phase D
+    // B: A1 = B @ W1 (layout [H][EC]); H1 = silu(A1) lives in the staging area until
+    // phase D.  Thread (j, edge group): hidden unit j for EPT consecutive edges.
     float* s_A1 = smem + L.A1;
     float* s_A2 = smem + L.A2;
     float* s_H2 = smem + L.H2;
     float* s_H1 = smem + L.stage;
-    for (int i = t; i < H * EC; i += CONV_THREADS) {     // i: storage position of (j, e)
-        int j, e;
-        hk_inv<H>(i, j, e);
-        float a = 0.0f;
-        for (int n = 0; n < D.n_basis; ++n) a = fmaf(s_B[n * EC + e], __ldg(W1 + n * H + j), a);
-        s_A1[i] = a;
-        s_H1[i] = siluf_(a);
+    {
+        constexpr int EPT = EC * H / CONV_THREADS;
+        static_assert(EPT == 4 || EPT == 2, "edges per thread of the input layer");
+        static_assert(H / 8 <= CONV_WARPS, "one hidden n tile per warp");
+        const int j = t % H, e0 = (t / H) * EPT;
+        float a[EPT];
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) a[q] = 0.0f;
+        for (int n = 0; n < D.n_basis; ++n) {
+            const float wv = smem[L.W1 + n * H + j];
+            const float* bn = s_B + n * EC + e0;
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) a[q] = fmaf(bn[q], wv, a[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const int o = hk<H>(j, e0 + q);
+            s_A1[o] = a[q];
+            s_H1[o] = siluf_(a[q]);
+        }
     }
     // C: G matrices (independent of B)
     float* s_G = smem + L.G;
@@ -408,10 +450,13 @@ __device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem
     }
     __syncthreads();
     if constexpr (BF) {          // A2 = H1 @ W2 on tensor cores, H2 = silu(A2)
-        const int warp = t >> 5, lane = t & 31, g = lane >> 2, tq = lane & 3;
-        for (int nt = warp; nt < H / 8; nt += CONV_WARPS) {
+        const int lane = t & 31, g = lane >> 2, tq = lane & 3;
+        if (warp < H / 8) {
+            const int nt = warp;
             float c[4];
-            hidden_mma<H>(s_H1, W2T_h, c, nt);
+            HiddenB<H> hb;
+            hidden_load<H>(W2T_h, nt, hb);
+            hidden_mma<H>(s_H1, hb, c);
             const int j = nt * 8 + 2 * tq;
             const int o[4] = {hk<H>(j, g), hk<H>(j + 1, g), hk<H>(j, g + 8), hk<H>(j + 1, g + 8)};
 #pragma unroll

@@ -178,12 +178,13 @@ conv_fwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
     const int* s_src = reinterpret_cast<const int*>(smem + L.src);
     const int* s_dst = reinterpret_cast<const int*>(smem + L.dst);
     const int* s_first = reinterpret_cast<const int*>(smem + L.first);
+    load_W1<H>(D, L, smem, W1);
     EdgePrefetch pf;
     pf.fetch(E0, E1, dst, src, geom, row_ptr);
     for (int c0 = E0; c0 < E1; c0 += EC) {
         const int ne = min(EC, E1 - c0);
         __syncthreads();
-        chunk_prologue<H, BF>(D, L, smem, c0, ne, pf, W1, W2, W2T_h);
+        chunk_prologue<H, BF>(D, L, smem, c0, ne, pf, W2, W2T_h);
         pf.fetch(c0 + EC, E1, dst, src, geom, row_ptr);   // next chunk's edges, in flight meanwhile
         if constexpr (BF) chunk_w_gemm_bf16<H>(D, L, smem, W3T_h);
         else chunk_w_gemm_f32<H>(D, L, smem, W3);
