@@ -8,6 +8,12 @@ resident in HBM.  metric: atom-steps/s (higher is better).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
   python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
+  python bench.py --workload sio2_3000 --precision fp32 --md-steps 100
+  python bench.py --workload si3n4_112000 --md-steps 1000
+      NVE velocity-Verlet MD through sevennet_md_step (1 fs, Maxwell-Boltzmann
+      velocities at 3000 K); a step is one evaluation with its neighbour rebuild
+      plus the position and velocity update; reports atom-steps/s and the drift
+      of the total energy.
 
 Under torchrun (N > 1) every rank evaluates its own replica (the evaluation
 does not shard: replicas only); value = all ranks' atom-steps / the slowest
@@ -236,6 +242,49 @@ def serving_run(sn, model, precision, n_requests=512, rate_hz=200.0, budget_gb=8
                      f"Poisson arrivals at {rate_hz:.0f}/s"}
 
 
+# initial-velocity seeds of the MD workloads (3000 K)
+MD_VEL_SEED = {"sio2_3000": 3, "si3n4_112000": 8}
+
+
+def md_run(args, world, rank, dev, sn, model, s):
+    """NVE MD through the C ABI: atom-steps/s and total-energy drift."""
+    import numpy as np
+    import torch
+    from synth import maxwell_boltzmann
+    from synth.configs import MASSES_AMU
+    masses = np.asarray(MASSES_AMU)
+    vel = maxwell_boltzmann(masses[s.species], 3000.0, seed=MD_VEL_SEED.get(args.workload, 3))
+    md = sn.MD(model, s.pos, vel, s.species, masses, s.cell, args.precision)
+    md.step(args.warmup, 1.0)
+    clk = ClockSampler(dev.index)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clk.start()
+    t0 = time.perf_counter()
+    ep, ek = md.step(args.md_steps, 1.0)
+    torch.cuda.synchronize(dev)
+    wall = max_over_ranks(time.perf_counter() - t0, world, dev)
+    clk.stop()
+    etot = ep + ek
+    n = s.n_atoms
+    line = {"metric": "atom-steps/s (NVE MD: neighbour rebuild + E+F+virial + Verlet update)",
+            "value": world * n * args.md_steps / wall, "unit": UNIT, "n_gpus": world, "steps": args.md_steps,
+            "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.md_steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16+f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n_atoms": n, "precision": args.precision, "dt_fs": 1.0,
+                       "T0_K": 3000.0, "timing": "host wall clock around sevennet_md_step",
+                       "parallelism": f"replicas x{world}"},
+            "md": {"epot0_eV_per_atom": float(ep[0] / n), "ekin0_eV_per_atom": float(ek[0] / n),
+                   "etot_drift_eV_per_atom": float((etot[-1] - etot[0]) / n),
+                   "etot_max_dev_eV_per_atom": float(np.max(np.abs(etot - etot[0])) / n),
+                   "finite": bool(np.all(np.isfinite(etot)))},
+            "clocks": clk.summary()}
+    md.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -264,6 +313,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream measurement")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--md-steps", type=int, default=0, help="run NVE MD for this many timed steps instead")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -281,6 +331,9 @@ def main():
     s, spec = make_workload(args.workload)
     weights = normal_weights(sn.n_params(spec))
     model = sn.SevenNet(spec, weights, device=local)
+    if args.md_steps > 0:
+        md_run(args, world, rank, dev, sn, model, s)
+        return
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     species = torch.tensor(s.species, dtype=torch.int32, device=dev)
     pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
