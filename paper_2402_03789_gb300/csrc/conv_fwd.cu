@@ -5,6 +5,10 @@
 
 namespace sn {
 
+// Forward gathers: a rolling one-edge-ahead prefetch (one copy of the edge
+// body) or PF edges unrolled together.
+constexpr bool FWD_ROLL = false;
+
 template <int L1, int LMAX, int KIND>
 struct FwdSets {
     static constexpr PathSets sets = fwd_path_sets(L1, LMAX, KIND);
@@ -74,50 +78,69 @@ __device__ __forceinline__ void tp_fwd_set(const ConvDesc& D, int u0, int ne, co
                 for (int c = 0; c < decltype(n3)::value; ++c) mw[c * mm + 32 * k] = acc[k][off + c];
         });
     };
-    for (int e0 = 0; e0 < ne; e0 += PF) {
-        float xv[PF][CPL][N1];
-#pragma unroll
-        for (int q = 0; q < PF; ++q) {
-            const int e = min(e0 + q, ne - 1);
-            const float* xr = xb + (size_t)s_src[e] * x_dim;
+    // per edge: the running sums of every path of the set, for CPL channels
+    auto edge = [&](int e, const float (&xv)[CPL][N1]) {
+        const int v = s_dst[e];
+        if (v != cur) {
+            flush(cur);
+            cur = v;
 #pragma unroll
             for (int k = 0; k < CPL; ++k)
 #pragma unroll
-                for (int a = 0; a < N1; ++a) xv[q][k][a] = __ldg(xr + a * mul + 32 * k);
+                for (int c = 0; c < NACC; ++c) acc[k][c] = 0.0f;
         }
+        static_for<NP>([&](auto I) {
+            constexpr int i = I0 + decltype(I)::value;
+            constexpr int N3 = 2 * BP::list.l3[i] + 1;
+            constexpr int off = fwd_acc_off<L1, LMAX, KIND>(J, i);
+            const PathDesc& P = D.paths[BP::begin + i];
+            float G[((N1 * N3 + 3) / 4) * 4];
+            load_G<N1 * N3>(s_G + e * nG + P.g_off, G);
+            const float* wr = s_w + e * Wpad + P.col0 + u0;
 #pragma unroll
-        for (int q = 0; q < PF; ++q) {
-            const int e = e0 + q;
-            if (e >= ne) break;
-            const int v = s_dst[e];
-            if (v != cur) {
-                flush(cur);
-                cur = v;
+            for (int k = 0; k < CPL; ++k) {
+                const float wv = wr[32 * k];
 #pragma unroll
-                for (int k = 0; k < CPL; ++k)
+                for (int c = 0; c < N3; ++c) {
+                    float tt = 0.0f;
 #pragma unroll
-                    for (int c = 0; c < NACC; ++c) acc[k][c] = 0.0f;
-            }
-            static_for<NP>([&](auto I) {
-                constexpr int i = I0 + decltype(I)::value;
-                constexpr int N3 = 2 * BP::list.l3[i] + 1;
-                constexpr int off = fwd_acc_off<L1, LMAX, KIND>(J, i);
-                const PathDesc& P = D.paths[BP::begin + i];
-                float G[((N1 * N3 + 3) / 4) * 4];
-                load_G<N1 * N3>(s_G + e * nG + P.g_off, G);
-                const float* wr = s_w + e * Wpad + P.col0 + u0;
-#pragma unroll
-                for (int k = 0; k < CPL; ++k) {
-                    const float wv = wr[32 * k];
-#pragma unroll
-                    for (int c = 0; c < N3; ++c) {
-                        float tt = 0.0f;
-#pragma unroll
-                        for (int a = 0; a < N1; ++a) tt = fmaf(xv[q][k][a], G[a * N3 + c], tt);
-                        acc[k][off + c] = fmaf(wv, tt, acc[k][off + c]);
-                    }
+                    for (int a = 0; a < N1; ++a) tt = fmaf(xv[k][a], G[a * N3 + c], tt);
+                    acc[k][off + c] = fmaf(wv, tt, acc[k][off + c]);
                 }
-            });
+            }
+        });
+    };
+    auto gather = [&](int e, float (&xv)[CPL][N1]) {
+        const float* xr = xb + (size_t)s_src[e] * x_dim;
+#pragma unroll
+        for (int k = 0; k < CPL; ++k)
+#pragma unroll
+            for (int a = 0; a < N1; ++a) xv[k][a] = __ldg(xr + a * mul + 32 * k);
+    };
+    if constexpr (FWD_ROLL) {
+        // one copy of the edge body; the next edge's gathers are in flight meanwhile
+        float xn[CPL][N1];
+        if (ne > 0) gather(0, xn);
+#pragma unroll 1
+        for (int e = 0; e < ne; ++e) {
+            float xv[CPL][N1];
+#pragma unroll
+            for (int k = 0; k < CPL; ++k)
+#pragma unroll
+                for (int a = 0; a < N1; ++a) xv[k][a] = xn[k][a];
+            if (e + 1 < ne) gather(e + 1, xn);
+            edge(e, xv);
+        }
+    } else {
+        for (int e0 = 0; e0 < ne; e0 += PF) {
+            float xv[PF][CPL][N1];
+#pragma unroll
+            for (int q = 0; q < PF; ++q) gather(min(e0 + q, ne - 1), xv[q]);
+#pragma unroll
+            for (int q = 0; q < PF; ++q) {
+                if (e0 + q >= ne) break;
+                edge(e0 + q, xv[q]);
+            }
         }
     }
     if (ne > 0) flush(cur);

@@ -101,13 +101,14 @@ __host__ __device__ constexpr int path_begin(int l1, int lmax, int kind) {
 }
 
 // Forward convolution work sets: the path list of one input irrep l1 split into
-// contiguous subsets of at most fwd_set_cap(kind) multiply-adds per channel and
-// edge (a path costs (2 l1 + 1)(2 l3 + 1) for x G and 2 l3 + 1 for the weight).
-// One set shares the gather of x_src[l1] over its paths; its running sums stay
-// in registers.  The first block (scalar input only) uses small sets so that its
-// few paths still give every warp work.
+// contiguous subsets of at most fwd_set_cap(kind) multiply-adds per channel
+// and edge (a path costs (2 l1 + 1)(2 l3 + 1) for x G and 2 l3 + 1 for the
+// weight).  One set shares the gather of x_src[l1] over its paths; its running
+// sums stay in registers.  Large sets cut gathers and code; the first block
+// (scalar input only) uses small sets so that its few paths still give every
+// warp work.
 constexpr int FWD_MAX_SETS = 6;
-__host__ __device__ constexpr int fwd_set_cap(int kind) { return (kind & 1) ? 8 : 48; }
+__host__ __device__ constexpr int fwd_set_cap(int kind) { return (kind & 1) ? 8 : 96; }
 
 struct PathSets {
     int n;          // number of sets
