@@ -203,7 +203,7 @@ struct GemmProb {
     const __nv_bfloat16* Bh;   // [N][K] BF16 transpose (hi), followed by the lo term at Bh + K*N
     float* C;
     int64_t n_atoms;
-    int32_t R, K, N;
+    int32_t R, K, N;           // K and N are multiples of 32 (every multiplicity is)
     int32_t lda, a_off, ldc, c_off;
     int32_t accumulate;        // 1: C += A B, 0: C = A B
 };

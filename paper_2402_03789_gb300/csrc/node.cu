@@ -87,9 +87,8 @@ gemm_f32_kernel(const GemmBatch batch) {
 }
 
 // ---------------------------------------------------------------- BF16 GEMM
-// Tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulate).  64 x 64
-// tile, 8 warps as 4 (rows) x 2 (cols), each warp 16 rows x 32 cols.  A is
-// read as FP32 and rounded to BF16 in the fragment; B is the BF16 [N][K] copy.
+// Tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulate).  A is read
+// as FP32 and rounded to BF16 in the fragment; B is the BF16 [N][K] copy.
 // Activations and weights both enter as hi + lo BF16 pairs; three MMAs
 // (hi*hi, lo*hi, hi*lo) keep about 16 mantissa bits of each operand.
 constexpr bool GEMM_SPLIT_ACT = true;
@@ -110,71 +109,100 @@ __device__ __forceinline__ void mma_bf16_n(float* c, const uint32_t* a, const ui
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// 128 x 64 output tile, 8 warps as 4 (rows) x 2 (cols), each warp 32 rows x 32
+// cols (2 m tiles x 4 n tiles).  K runs in blocks of 32 under one k permutation
+// of both operands (the reduction order inside an MMA is free): lane tq owns
+// k = kb + 8 tq + [0, 8), k step ks takes kb + 8 tq + 4 ks + [0, 4).  Its A
+// values are then one float4 per row and k step, and its B words (hi and lo)
+// one 16-byte load per n row and k block.  K and N are multiples of 32.
 __global__ void __launch_bounds__(256)
 gemm_bf16_kernel(const GemmBatch batch) {
     const GemmProb& P = batch.p[blockIdx.z];
     const int64_t rows = P.n_atoms * P.R;
-    const int64_t r0 = (int64_t)blockIdx.x * 64;
+    const int64_t r0 = (int64_t)blockIdx.x * 128;
     const int n0 = blockIdx.y * 64;
     if (r0 >= rows || n0 >= P.N) return;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tq = lane & 3;
     const int wr = warp & 3, wc = warp >> 2;
     const int nbase = n0 + wc * 32;
     if (nbase >= P.N) return;
-    const int64_t ra = r0 + wr * 16 + g, rb = ra + 8;
     auto rowptr = [&](int64_t r) -> const float* {
         if (r >= rows) return nullptr;
         const int64_t v = r / P.R;
         const int mm = (int)(r % P.R);
         return P.A + v * P.lda + P.a_off + (int64_t)mm * P.K;
     };
-    const float* pa = rowptr(ra);
-    const float* pb = rowptr(rb);
-    float c[4][4];
+    const float* pr[2][2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.0f;
-    const float2 z = make_float2(0.f, 0.f);
-    for (int k0 = 0; k0 < P.K; k0 += 16) {
-        const int kk = k0 + 2 * tq;
-        const float2 x0 = pa ? *reinterpret_cast<const float2*>(pa + kk) : z;
-        const float2 x1 = pb ? *reinterpret_cast<const float2*>(pb + kk) : z;
-        const float2 x2 = pa ? *reinterpret_cast<const float2*>(pa + kk + 8) : z;
-        const float2 x3 = pb ? *reinterpret_cast<const float2*>(pb + kk + 8) : z;
-        uint32_t a[4], al[4];
-        split_bf16_n(x0.x, x0.y, a[0], al[0]);
-        split_bf16_n(x1.x, x1.y, a[1], al[1]);
-        split_bf16_n(x2.x, x2.y, a[2], al[2]);
-        split_bf16_n(x3.x, x3.y, a[3], al[3]);
-        const int64_t lo_off = (int64_t)P.K * P.N / 2;     // in 32-bit words
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) pr[mt][h] = rowptr(r0 + wr * 32 + mt * 16 + h * 8 + g);
+    float c[2][4][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) c[mt][j][0] = c[mt][j][1] = c[mt][j][2] = c[mt][j][3] = 0.0f;
+    const int64_t lo_off = (int64_t)P.K * P.N;          // bf16 elements
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int kb = 0; kb < P.K; kb += 32) {
+        uint4 bh[4], bl[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const uint32_t* brow = reinterpret_cast<const uint32_t*>(P.Bh + (int64_t)(nbase + j * 8 + g) * P.K);
-            const uint32_t b[2] = {__ldg(brow + (kk >> 1)), __ldg(brow + ((kk + 8) >> 1))};
-            const uint32_t bl[2] = {__ldg(brow + lo_off + (kk >> 1)), __ldg(brow + lo_off + ((kk + 8) >> 1))};
-            mma_bf16_n(c[j], a, b);
-            if (GEMM_SPLIT_ACT) mma_bf16_n(c[j], al, b);
-            mma_bf16_n(c[j], a, bl);
+            const __nv_bfloat16* br = P.Bh + (int64_t)(nbase + j * 8 + g) * P.K + kb + 8 * tq;
+            bh[j] = __ldg(reinterpret_cast<const uint4*>(br));
+            bl[j] = __ldg(reinterpret_cast<const uint4*>(br + lo_off));
         }
-    }
+        float4 av[2][2][2];                                // [m tile][row half][k step]
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        const int64_t r = half ? rb : ra;
-        if (r >= rows) continue;
-        const int64_t v = r / P.R;
-        const int mm = (int)(r % P.R);
-        float* cp = P.C + v * P.ldc + P.c_off + (int64_t)mm * P.N;
+        for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int col = nbase + j * 8 + 2 * tq;
-            float2 o = make_float2(c[j][2 * half], c[j][2 * half + 1]);
-            if (P.accumulate) {
-                const float2 q = *reinterpret_cast<const float2*>(cp + col);
-                o.x += q.x;
-                o.y += q.y;
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks)
+                    av[mt][h][ks] = pr[mt][h] ? *reinterpret_cast<const float4*>(pr[mt][h] + kb + 8 * tq + 4 * ks) : z4;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                uint32_t a[4], al[4];
+                split_bf16_n(av[mt][0][ks].x, av[mt][0][ks].y, a[0], al[0]);
+                split_bf16_n(av[mt][1][ks].x, av[mt][1][ks].y, a[1], al[1]);
+                split_bf16_n(av[mt][0][ks].z, av[mt][0][ks].w, a[2], al[2]);
+                split_bf16_n(av[mt][1][ks].z, av[mt][1][ks].w, a[3], al[3]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t* wh = reinterpret_cast<const uint32_t*>(&bh[j]);
+                    const uint32_t* wl = reinterpret_cast<const uint32_t*>(&bl[j]);
+                    const uint32_t b[2] = {wh[2 * ks], wh[2 * ks + 1]};
+                    const uint32_t b2[2] = {wl[2 * ks], wl[2 * ks + 1]};
+                    mma_bf16_n(c[mt][j], a, b);
+                    if (GEMM_SPLIT_ACT) mma_bf16_n(c[mt][j], al, b);
+                    mma_bf16_n(c[mt][j], a, b2);
+                }
             }
-            *reinterpret_cast<float2*>(cp + col) = o;
         }
     }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t r = r0 + wr * 32 + mt * 16 + h * 8 + g;
+            if (r >= rows) continue;
+            const int64_t v = r / P.R;
+            const int mm = (int)(r % P.R);
+            float* cp = P.C + v * P.ldc + P.c_off + (int64_t)mm * P.N;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int col = nbase + j * 8 + 2 * tq;
+                float2 o = make_float2(c[mt][j][2 * h], c[mt][j][2 * h + 1]);
+                if (P.accumulate) {
+                    const float2 q = *reinterpret_cast<const float2*>(cp + col);
+                    o.x += q.x;
+                    o.y += q.y;
+                }
+                *reinterpret_cast<float2*>(cp + col) = o;
+            }
+        }
 }
 
 void launch_gemm(const GemmBatch& b, sevennet_precision prec, cudaStream_t st) {
@@ -186,9 +214,13 @@ void launch_gemm(const GemmBatch& b, sevennet_precision prec, cudaStream_t st) {
         max_n = std::max(max_n, b.p[i].N);
     }
     if (max_rows == 0) return;
-    dim3 grid((unsigned)((max_rows + 63) / 64), (unsigned)((max_n + 63) / 64), (unsigned)b.n);
-    if (prec == SEVENNET_BF16) gemm_bf16_kernel<<<grid, 256, 0, st>>>(b);
-    else gemm_f32_kernel<<<grid, 256, 0, st>>>(b);
+    if (prec == SEVENNET_BF16) {
+        const dim3 grid((unsigned)((max_rows + 127) / 128), (unsigned)((max_n + 63) / 64), (unsigned)b.n);
+        gemm_bf16_kernel<<<grid, 256, 0, st>>>(b);
+    } else {
+        const dim3 grid((unsigned)((max_rows + 63) / 64), (unsigned)((max_n + 63) / 64), (unsigned)b.n);
+        gemm_f32_kernel<<<grid, 256, 0, st>>>(b);
+    }
 }
 
 // ---------------------------------------------------------------- embedding
