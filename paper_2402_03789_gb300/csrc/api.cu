@@ -338,6 +338,7 @@ sevennet_status ws_reserve(sevennet_model* M, Workspace* ws, int64_t n_atoms, in
         SN_TRY(ws_alloc(ws, &ws->struct_of, N));
         SN_TRY(ws_alloc(ws, &ws->pos_s, N * 3));
         SN_TRY(ws_alloc(ws, &ws->frac_floor, N * 3));
+        SN_TRY(ws_alloc(ws, &ws->q32, N));
         SN_TRY(ws_alloc(ws, &ws->species_s, N));
         SN_TRY(ws_alloc(ws, &ws->row_ptr, N + 1));
         SN_TRY(ws_alloc(ws, &ws->row_cnt, N + 1));

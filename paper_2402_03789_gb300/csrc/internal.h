@@ -282,8 +282,9 @@ struct Workspace {
     int* bin_fill = nullptr;      // [bins]
     int* perm = nullptr;          // [N] internal -> input index
     int* struct_of = nullptr;     // [N] internal atom -> structure
-    double* pos_s = nullptr;      // [N][3] positions in internal order (as given)
+    double* pos_s = nullptr;      // [N][3] wrapped positions in internal order
     double* frac_floor = nullptr; // [N][3] integer image of each internal atom
+    float4* q32 = nullptr;        // [N] wrapped positions in FP32 (distance pre-test)
     int* species_s = nullptr;     // [N]
     int* row_ptr = nullptr;       // [N+1]
     int* row_cnt = nullptr;       // [N+1]

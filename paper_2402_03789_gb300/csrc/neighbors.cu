@@ -119,12 +119,14 @@ __global__ void sort_bins_kernel(int64_t n_bins, const int* __restrict__ bin_sta
     }
 }
 
-// Gather positions/species into internal order; wrapped positions and images.
+// Gather species into internal order, with the wrapped position q = p - n cell and
+// the integer image n of every atom (n = floor of the fractional coordinate along
+// periodic directions).
 __global__ void gather_kernel(int64_t n, int S, const int64_t* __restrict__ atom_off,
                               const int* __restrict__ sdesc, const double* __restrict__ cells,
                               const double* __restrict__ inv_cells, const int* __restrict__ perm,
                               const double* __restrict__ pos, const int32_t* __restrict__ species,
-                              double* __restrict__ pos_s, double* __restrict__ fl_s,
+                              double* __restrict__ pos_s, double* __restrict__ fl_s, float4* __restrict__ q32,
                               int* __restrict__ species_s, int* __restrict__ struct_of) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -133,48 +135,68 @@ __global__ void gather_kernel(int64_t n, int S, const int64_t* __restrict__ atom
     const int* d = sdesc + s * SD;
     const double* ic = inv_cells + s * 9;
     const double p[3] = {pos[o * 3], pos[o * 3 + 1], pos[o * 3 + 2]};
+    double fl[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        pos_s[i * 3 + a] = p[a];
         double f = p[0] * ic[0 * 3 + a] + p[1] * ic[1 * 3 + a] + p[2] * ic[2 * 3 + a];
-        fl_s[i * 3 + a] = d[6 + a] ? floor(f) : 0.0;
+        fl[a] = d[6 + a] ? floor(f) : 0.0;
+        fl_s[i * 3 + a] = fl[a];
     }
+    const double* c = cells + s * 9;
+    double q[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {     // wrapped position q = p - fl cell
+        q[a] = p[a] - (fl[0] * c[0 * 3 + a] + fl[1] * c[1 * 3 + a] + fl[2] * c[2 * 3 + a]);
+        pos_s[i * 3 + a] = q[a];
+    }
+    q32[i] = make_float4((float)q[0], (float)q[1], (float)q[2], 0.0f);
     species_s[i] = species[o];
     struct_of[i] = s;
 }
 
-// Visit every neighbour (w, S~) of internal atom v in a fixed order.
-// Wrapped position q = p - n cell, n = fl.  d = q_w - q_v + S~ cell.
-template <typename F>
-__device__ __forceinline__ void visit_neighbors(int64_t v, const int* __restrict__ sdesc,
-                                                const double* __restrict__ cells,
-                                                const int* __restrict__ struct_of,
-                                                const int* __restrict__ bin_start,
-                                                const double* __restrict__ pos_s,
-                                                const double* __restrict__ fl_s, double rc2, F f) {
+// Count (FILL = false) or write (FILL = true) the edges of every internal atom
+// v.  A group of NGL lanes serves one receiver: it scans the bins within the
+// search range in a fixed order, the members of a bin in order, NGL candidates
+// at a time; a ballot over the group gives each hit its slot, so the edge order
+// is the serial one (bin order, then member order).  d = q_w - q_v + S~ cell,
+// with q the wrapped positions; the edge's shift is S~ - n_w + n_v.  The test
+// that decides an edge is FP64.  An FP32 pre-test skips the FP64 work for
+// candidates clearly outside r_c; its margin, 1e-3 A + 1e-6 (|q_v| + |S~ cell| +
+// r_c), is over ten times the FP32 rounding of d for any coordinates (positions
+// along non-periodic directions are not wrapped), so it cannot drop an edge.
+constexpr int NGL = 8;
+
+__device__ __forceinline__ int floor_div(int a, int n) { return a >= 0 ? a / n : -((n - 1 - a) / n); }
+
+template <bool FILL>
+__global__ void __launch_bounds__(128)
+edges_kernel(int64_t n, double rc2, float rc32, int64_t cap, const int* __restrict__ sdesc,
+             const double* __restrict__ cells, const int* __restrict__ struct_of, const int* __restrict__ bin_start,
+             const double* __restrict__ q_s, const float4* __restrict__ q32, const double* __restrict__ fl_s,
+             const int* __restrict__ row_ptr,
+             int* __restrict__ counts, int* __restrict__ flags, int* __restrict__ dst, int* __restrict__ src,
+             int* __restrict__ shift, float4* __restrict__ geom) {
+    const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / NGL;
+    if (v >= n) return;                                    // the whole group leaves together
+    const int j = threadIdx.x & (NGL - 1);
+    const int gsh = threadIdx.x & 31 & ~(NGL - 1);
+    const unsigned gmask = ((1u << NGL) - 1) << gsh;
     const int s = struct_of[v];
     const int* d = sdesc + s * SD;
     const double* c = cells + s * 9;
-    double q[3];
-    const double fv[3] = {fl_s[v * 3], fl_s[v * 3 + 1], fl_s[v * 3 + 2]};
+    const double qv[3] = {q_s[v * 3], q_s[v * 3 + 1], q_s[v * 3 + 2]};
+    const float4 qv32 = q32[v];
+    const float qmag = fmaxf(fabsf(qv32.x), fmaxf(fabsf(qv32.y), fabsf(qv32.z)));
+    float c32[9];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-        q[a] = pos_s[v * 3 + a] - (fv[0] * c[0 * 3 + a] + fv[1] * c[1 * 3 + a] + fv[2] * c[2 * 3 + a]);
-    // bin of v, recomputed from its wrapped fractional coordinate
-    // (the same as at binning: the bins are what bin_start indexes)
+    for (int a = 0; a < 9; ++a) c32[a] = (float)c[a];
     int bv[3];
-    {
-        // locate the bin by searching bin_start is not possible; recompute instead
-        const double* cc = c;
-        (void)cc;
-    }
-    // we store the bin of internal atoms implicitly: find it by binary search
     {
         const int base = d[9];
         const int nb = d[0] * d[1] * d[2];
         int lo = base, hi = base + nb;   // largest b with bin_start[b] <= v
         while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
+            const int mid = (lo + hi) >> 1;
             if (bin_start[mid] <= v) lo = mid; else hi = mid;
         }
         const int local = lo - base;
@@ -182,79 +204,74 @@ __device__ __forceinline__ void visit_neighbors(int64_t v, const int* __restrict
         bv[1] = (local / d[2]) % d[1];
         bv[0] = local / (d[2] * d[1]);
     }
+    int64_t e = FILL ? (int64_t)row_ptr[v] : 0;
+    bool close = false;
     for (int ox = -d[3]; ox <= d[3]; ++ox) {
         int bx = bv[0] + ox, sx = 0;
-        if (d[6]) { sx = (int)floor((double)bx / d[0]); bx -= sx * d[0]; }
+        if (d[6]) { sx = floor_div(bx, d[0]); bx -= sx * d[0]; }
         else if (bx < 0 || bx >= d[0]) continue;
         for (int oy = -d[4]; oy <= d[4]; ++oy) {
             int by = bv[1] + oy, sy = 0;
-            if (d[7]) { sy = (int)floor((double)by / d[1]); by -= sy * d[1]; }
+            if (d[7]) { sy = floor_div(by, d[1]); by -= sy * d[1]; }
             else if (by < 0 || by >= d[1]) continue;
             for (int oz = -d[5]; oz <= d[5]; ++oz) {
                 int bz = bv[2] + oz, sz = 0;
-                if (d[8]) { sz = (int)floor((double)bz / d[2]); bz -= sz * d[2]; }
+                if (d[8]) { sz = floor_div(bz, d[2]); bz -= sz * d[2]; }
                 else if (bz < 0 || bz >= d[2]) continue;
                 const int b = d[9] + (bx * d[1] + by) * d[2] + bz;
-                const double sh[3] = {
-                    sx * c[0] + sy * c[3] + sz * c[6],
-                    sx * c[1] + sy * c[4] + sz * c[7],
-                    sx * c[2] + sy * c[5] + sz * c[8]};
-                for (int w = bin_start[b]; w < bin_start[b + 1]; ++w) {
-                    const double fw[3] = {fl_s[w * 3], fl_s[w * 3 + 1], fl_s[w * 3 + 2]};
-                    double dd[3];
+                const float fx = (float)sx, fy = (float)sy, fz = (float)sz;
+                const float sh32[3] = {fx * c32[0] + fy * c32[3] + fz * c32[6],
+                                       fx * c32[1] + fy * c32[4] + fz * c32[7],
+                                       fx * c32[2] + fy * c32[5] + fz * c32[8]};
+                const float smag = fmaxf(fabsf(sh32[0]), fmaxf(fabsf(sh32[1]), fabsf(sh32[2])));
+                const float rpre = rc32 + 1e-3f + 1e-6f * (qmag + smag + rc32);
+                const float rc2_pre = rpre * rpre;
+                const int w1 = bin_start[b + 1];
+                for (int w0 = bin_start[b]; w0 < w1; w0 += NGL) {
+                    const int w = w0 + j;
+                    bool hit = false;
+                    double dd[3], r2 = 0.0;
+                    if (w < w1) {
+                        const float4 qw = q32[w];
+                        const float ex = qw.x - qv32.x + sh32[0], ey = qw.y - qv32.y + sh32[1],
+                                    ez = qw.z - qv32.z + sh32[2];
+                        if (ex * ex + ey * ey + ez * ez < rc2_pre) {
+                            const double sh[3] = {
+                                sx * c[0] + sy * c[3] + sz * c[6],
+                                sx * c[1] + sy * c[4] + sz * c[7],
+                                sx * c[2] + sy * c[5] + sz * c[8]};
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        const double qw = pos_s[w * 3 + a] -
-                                          (fw[0] * c[0 * 3 + a] + fw[1] * c[1 * 3 + a] + fw[2] * c[2 * 3 + a]);
-                        dd[a] = qw - q[a] + sh[a];
+                            for (int a = 0; a < 3; ++a) dd[a] = q_s[w * 3 + a] - qv[a] + sh[a];
+                            r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+                            const bool self = (w == v) && sx == 0 && sy == 0 && sz == 0;
+                            hit = !self && r2 < rc2;
+                        }
                     }
-                    const double r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
-                    const bool self = (w == v) && sx == 0 && sy == 0 && sz == 0;
-                    if (!self && r2 < rc2) f(w, sx, sy, sz, fw, fv, dd, r2);
+                    const unsigned mine = (__ballot_sync(gmask, hit) >> gsh) & ((1u << NGL) - 1);
+                    if constexpr (FILL) {
+                        if (hit) {
+                            const int64_t slot = e + __popc(mine & ((1u << j) - 1));
+                            if (slot < cap) {
+                                dst[slot] = (int)v;
+                                src[slot] = w;
+                                shift[slot * 3 + 0] = sx - (int)fl_s[w * 3 + 0] + (int)fl_s[v * 3 + 0];
+                                shift[slot * 3 + 1] = sy - (int)fl_s[w * 3 + 1] + (int)fl_s[v * 3 + 1];
+                                shift[slot * 3 + 2] = sz - (int)fl_s[w * 3 + 2] + (int)fl_s[v * 3 + 2];
+                                geom[slot] = make_float4((float)dd[0], (float)dd[1], (float)dd[2], (float)sqrt(r2));
+                            }
+                        }
+                    } else {
+                        if (hit && r2 < 1e-16) close = true;
+                    }
+                    e += __popc(mine);
                 }
             }
         }
     }
-}
-
-__global__ void count_edges_kernel(int64_t n, double rc2, const int* __restrict__ sdesc,
-                                   const double* __restrict__ cells, const int* __restrict__ struct_of,
-                                   const int* __restrict__ bin_start, const double* __restrict__ pos_s,
-                                   const double* __restrict__ fl_s, int* __restrict__ counts,
-                                   int* __restrict__ flags) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
-    int cnt = 0;
-    visit_neighbors(v, sdesc, cells, struct_of, bin_start, pos_s, fl_s, rc2,
-                    [&](int, int, int, int, const double*, const double*, const double*, double r2) {
-                        if (r2 < 1e-16) atomicOr(flags + 1, 1);
-                        ++cnt;
-                    });
-    counts[v] = cnt;
-}
-
-__global__ void fill_edges_kernel(int64_t n, double rc2, int64_t cap, const int* __restrict__ sdesc,
-                                  const double* __restrict__ cells, const int* __restrict__ struct_of,
-                                  const int* __restrict__ bin_start, const double* __restrict__ pos_s,
-                                  const double* __restrict__ fl_s, const int* __restrict__ row_ptr,
-                                  int* __restrict__ dst, int* __restrict__ src, int* __restrict__ shift,
-                                  float4* __restrict__ geom) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
-    int64_t e = row_ptr[v];
-    visit_neighbors(v, sdesc, cells, struct_of, bin_start, pos_s, fl_s, rc2,
-                    [&](int w, int sx, int sy, int sz, const double* fw, const double* fv,
-                        const double* dd, double r2) {
-                        if (e < cap) {
-                            dst[e] = (int)v;
-                            src[e] = w;
-                            shift[e * 3 + 0] = sx - (int)fw[0] + (int)fv[0];
-                            shift[e * 3 + 1] = sy - (int)fw[1] + (int)fv[1];
-                            shift[e * 3 + 2] = sz - (int)fw[2] + (int)fv[2];
-                            geom[e] = make_float4((float)dd[0], (float)dd[1], (float)dd[2], (float)sqrt(r2));
-                        }
-                        ++e;
-                    });
+    if constexpr (!FILL) {
+        if (j == 0) counts[v] = (int)e;
+        if (close) atomicOr(flags + 1, 1);
+    }
 }
 
 __global__ void reverse_kernel(int64_t n_edges, const int* __restrict__ row_ptr, const int* __restrict__ dst,
@@ -362,11 +379,11 @@ sevennet_status build_neighbors(sevennet_model* M, Workspace* ws, const BatchHos
         sort_bins_kernel<<<blocks_for(n_bins, 128), 128, 0, st>>>(n_bins, ws->bin_start, ws->perm);
         gather_kernel<<<blocks_for(N, 256), 256, 0, st>>>(N, S, ws->atom_off, ws->sdesc, ws->cells,
                                                          ws->inv_cells, ws->perm, pos_dev, species_dev,
-                                                         ws->pos_s, ws->frac_floor, ws->species_s,
+                                                         ws->pos_s, ws->frac_floor, ws->q32, ws->species_s,
                                                          ws->struct_of);
-        count_edges_kernel<<<blocks_for(N, 128), 128, 0, st>>>(N, rc * rc, ws->sdesc, ws->cells,
-                                                              ws->struct_of, ws->bin_start, ws->pos_s,
-                                                              ws->frac_floor, ws->row_cnt, ws->flags);
+        edges_kernel<false><<<blocks_for(N * NGL, 128), 128, 0, st>>>(
+            N, rc * rc, (float)rc, 0, ws->sdesc, ws->cells, ws->struct_of, ws->bin_start, ws->pos_s, ws->q32,
+            ws->frac_floor, nullptr, ws->row_cnt, ws->flags, nullptr, nullptr, nullptr, nullptr);
     }
     scan_kernel<<<1, 1024, 0, st>>>(ws->row_cnt, N, ws->row_ptr, ws->flags + 0);
     SN_CUDA(cudaMemcpyAsync(ws->flags_host, ws->flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -375,10 +392,9 @@ sevennet_status build_neighbors(sevennet_model* M, Workspace* ws, const BatchHos
     SN_CHECK(ws->flags_host[1] == 0, SEVENNET_EINVAL, "two atoms closer than 1e-8 A");
     if (E > ws->cap_edges) SN_TRY(ws_reserve(M, ws, N, E + E / 4 + 1024, n_bins, S, st));
     if (N > 0) {
-        fill_edges_kernel<<<blocks_for(N, 128), 128, 0, st>>>(N, rc * rc, ws->cap_edges, ws->sdesc, ws->cells,
-                                                             ws->struct_of, ws->bin_start, ws->pos_s,
-                                                             ws->frac_floor, ws->row_ptr, ws->dst, ws->src,
-                                                             ws->shift, ws->geom);
+        edges_kernel<true><<<blocks_for(N * NGL, 128), 128, 0, st>>>(
+            N, rc * rc, (float)rc, ws->cap_edges, ws->sdesc, ws->cells, ws->struct_of, ws->bin_start, ws->pos_s,
+            ws->q32, ws->frac_floor, ws->row_ptr, nullptr, ws->flags, ws->dst, ws->src, ws->shift, ws->geom);
     }
     if (E > 0)
         reverse_kernel<<<blocks_for(E, 256), 256, 0, st>>>(E, ws->row_ptr, ws->dst, ws->src, ws->shift,

@@ -68,9 +68,12 @@ def test_server_results_equal_single_evaluations():
         structs.append(random_structure(counts, float(rng.uniform(2.2, 3.1)), 1.5, seed=100 + k))
     srv = sn.Server(model, hbm_budget_bytes=2 << 30, n_streams=3, max_batch_structs=8, precision="fp32")
     tickets = []
-    for s in structs:
+    # a burst (queued faster than one evaluation takes, so later batches carry
+    # several structures), then arrivals spread out while batches are running
+    for i, s in enumerate(structs):
         tickets.append(srv.submit(s.pos, s.cell, s.species))
-        time.sleep(0.002)
+        if i >= 16:
+            time.sleep(0.002)
     results = {}
     t0 = time.time()
     while len(results) < len(tickets) and time.time() - t0 < 120:
