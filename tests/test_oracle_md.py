@@ -1,5 +1,8 @@
-"""Pins of the oracle integrator: NVE energy conservation of velocity Verlet
-and its second-order error (halving dt quarters the energy error)."""
+"""Pins of the oracle integrators: NVE energy conservation of velocity Verlet
+and its second-order error (halving dt quarters the energy error); the
+Nose-Hoover NVT splitting against velocity Verlet (tau -> infinity), its
+extended-energy conservation and second-order error, and the zero-force case
+against an independent ODE solution (scipy)."""
 
 import dataclasses
 
@@ -47,3 +50,54 @@ def test_verlet_error_is_second_order():
         errs.append(abs(ep[-1] + ek[-1] - etot0))
     ratio = errs[0] / errs[1]
     assert 2.5 < ratio < 6.0, (errs, ratio)
+
+
+def test_nose_hoover_reduces_to_verlet_for_infinite_tau():
+    s, spec, w, m, v = _setup(200.0)
+    p1, v1, *_ = oracle.velocity_verlet(spec, w, s.species, s.pos, v, m, s.cell, 1.0, 6)
+    out = oracle.nose_hoover_nvt(spec, w, s.species, s.pos, v, m, s.cell, 1.0, 6, 3000.0, 1e12)
+    assert np.abs(out[0] - p1).max() < 1e-10
+    assert np.abs(out[1] - v1).max() < 1e-12
+    assert abs(out[3]) < 1e-20 and abs(out[4]) < 1e-18          # xi, eta stay zero
+
+
+def test_nose_hoover_extended_energy_second_order():
+    s, spec, w, m, v = _setup(200.0)
+    errs = []
+    for dt, n in ((1.0, 8), (0.5, 16)):
+        out = oracle.nose_hoover_nvt(spec, w, s.species, s.pos, v, m, s.cell, dt, n, 1500.0, 10.0)
+        ex = out[7]
+        E0, *_ = oracle.energy_forces_virial(spec, w, s.species, s.pos, s.cell)
+        ex0 = E0 + oracle.kinetic_energy(v, m)
+        errs.append(abs(ex[-1] - ex0))
+        assert abs(out[3]) > 1e-4           # the thermostat acts (T0 != T)
+    ratio = errs[0] / errs[1]
+    assert 2.5 < ratio < 6.0, (errs, ratio)
+
+
+def test_nose_hoover_zero_forces_matches_ode():
+    # With F = 0 every velocity scales by exp(-eta), so K = K0 exp(-2 eta) and
+    # the thermostat obeys eta' = xi, xi' = (2 K0 exp(-2 eta) - N_f k T0) / Q.
+    from scipy.integrate import solve_ivp
+    rng = np.random.default_rng(11)
+    n = 64
+    m = rng.uniform(10.0, 30.0, n)
+    v = maxwell_boltzmann(m, 1000.0, seed=12)
+    pos = rng.uniform(0, 10, (n, 3))
+    t0k, tau, t_end = 3000.0, 10.0, 20.0
+    q = oracle.nose_hoover_q(n, t0k, tau)
+    nf, kt0 = 3 * n - 3, KB * t0k
+    k0 = oracle.kinetic_energy(v, m)
+
+    def rhs(_, y):
+        return [y[1], (2.0 * k0 * np.exp(-2.0 * y[0]) - nf * kt0) / q]
+    ref = solve_ivp(rhs, (0.0, t_end), [0.0, 0.0], rtol=1e-12, atol=1e-14).y[:, -1]
+    zero = lambda p: (0.0, np.zeros_like(p))
+    errs = []
+    for dt in (0.2, 0.1):
+        out = oracle.nose_hoover_steps(zero, pos, v, m, dt, int(round(t_end / dt)), t0k, tau)
+        errs.append(abs(out[4] - ref[0]))
+        assert abs(out[6][-1] - k0 * np.exp(-2.0 * ref[0])) < 1e-3 * k0
+        assert abs(out[3] - ref[1]) < 1e-3 * abs(ref[1]) + 1e-9
+    assert errs[1] < 1e-4 * abs(ref[0]) + 1e-9
+    assert 3.0 < errs[0] / errs[1] < 5.0, errs
