@@ -255,7 +255,12 @@ def md_run(args, world, rank, dev, sn, model, s):
     masses = np.asarray(MASSES_AMU)
     vel = maxwell_boltzmann(masses[s.species], 3000.0, seed=MD_VEL_SEED.get(args.workload, 3))
     md = sn.MD(model, s.pos, vel, s.species, masses, s.cell, args.precision)
+    if args.skin > 0:
+        md.set_skin(args.skin)
+    if args.nvt > 0:
+        md.set_nose_hoover(args.nvt, args.tau)
     md.step(args.warmup, 1.0)
+    builds0, _ = md.stats()
     clk = ClockSampler(dev.index)
     barrier(world)
     torch.cuda.synchronize(dev)
@@ -265,20 +270,31 @@ def md_run(args, world, rank, dev, sn, model, s):
     torch.cuda.synchronize(dev)
     wall = max_over_ranks(time.perf_counter() - t0, world, dev)
     clk.stop()
+    builds, _ = md.stats()
     etot = ep + ek
     n = s.n_atoms
-    line = {"metric": "atom-steps/s (NVE MD: neighbour rebuild + E+F+virial + Verlet update)",
+    ensemble = {"ensemble": "NVE"}
+    if args.nvt > 0:
+        xi, eta = md.nose_hoover()
+        kb = 8.617333262e-5
+        nf = 3 * n - 3
+        q = nf * kb * args.nvt * args.tau ** 2
+        ext = etot[-1] + 0.5 * q * xi * xi + nf * kb * args.nvt * eta
+        ensemble = {"ensemble": "NVT Nose-Hoover", "T0_K": args.nvt, "tau_fs": args.tau,
+                    "T_final_K": float(2 * ek[-1] / (nf * kb)), "extended_energy_final_eV": float(ext)}
+    line = {"metric": "atom-steps/s (MD: neighbour list + E+F+virial + Verlet update)",
             "value": world * n * args.md_steps / wall, "unit": UNIT, "n_gpus": world, "steps": args.md_steps,
             "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.md_steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16+f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "n_atoms": n, "precision": args.precision, "dt_fs": 1.0,
-                       "T0_K": 3000.0, "timing": "host wall clock around sevennet_md_step",
-                       "parallelism": f"replicas x{world}"},
+                       "T_init_K": 3000.0, "skin_A": args.skin, "timing": "host wall clock around sevennet_md_step",
+                       "parallelism": f"replicas x{world}"} | ensemble,
             "md": {"epot0_eV_per_atom": float(ep[0] / n), "ekin0_eV_per_atom": float(ek[0] / n),
                    "etot_drift_eV_per_atom": float((etot[-1] - etot[0]) / n),
                    "etot_max_dev_eV_per_atom": float(np.max(np.abs(etot - etot[0])) / n),
-                   "finite": bool(np.all(np.isfinite(etot)))},
+                   "finite": bool(np.all(np.isfinite(etot))),
+                   "neighbour_builds_in_timed_steps": int(builds - builds0)},
             "clocks": clk.summary()}
     md.close()
     if rank == 0:
@@ -313,7 +329,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream measurement")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--md-steps", type=int, default=0, help="run NVE MD for this many timed steps instead")
+    ap.add_argument("--md-steps", type=int, default=0, help="run MD for this many timed steps instead")
+    ap.add_argument("--skin", type=float, default=0.0, help="MD: Verlet-list skin in A (0: rebuild every step)")
+    ap.add_argument("--nvt", type=float, default=0.0, help="MD: Nose-Hoover target temperature in K (0: NVE)")
+    ap.add_argument("--tau", type=float, default=100.0, help="MD: Nose-Hoover time constant in fs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()

@@ -219,9 +219,11 @@ sevennet_status sevennet_conv_forward_noalloc(sevennet_model* model, int32_t lay
 sevennet_status sevennet_conv_dims(const sevennet_model* model, int32_t layer,
                                    int32_t* x_dim, int32_t* m_dim);
 
-/* Molecular dynamics: NVE velocity Verlet in FP64 on the device, neighbour
- * list rebuilt every step.  masses: amu per species [n_species]; vel A/fs.
- * Positions, velocities and forces stay on the device between steps. */
+/* Molecular dynamics: velocity Verlet in FP64 on the device (NVE by default),
+ * neighbour list rebuilt every step unless a skin is set.  masses: amu per
+ * species [n_species]; vel A/fs.  Positions, velocities and forces stay on the
+ * device between steps.  The paper drives its MD from LAMMPS (Sec. 3.2) with
+ * NVT runs in Sec. 4 and a melt-quench in Sec. 5.2. */
 sevennet_status sevennet_md_create(sevennet_model* model, int64_t n_atoms,
                                    const int32_t* species, const double* pos,
                                    const double* vel, const double* masses,
@@ -235,6 +237,29 @@ sevennet_status sevennet_md_step(sevennet_md* md, int64_t n_steps, double dt_fs,
 /* Host copies of the current state (each may be NULL). */
 sevennet_status sevennet_md_get_state(const sevennet_md* md, double* pos, double* vel,
                                       double* forces);
+/* Verlet list with a skin (A, >= 0; 0 = rebuild every step, the default).
+ * With skin > 0 the neighbour list is built for r_c + skin and reused: each
+ * step keeps its pairs within r_c at the current positions (same edge set as a
+ * full build, in list order), and a new list is built once an atom has moved
+ * more than skin / 2 since the last build.  The energy, forces and virial are
+ * those of the full build up to FP summation order.  EINVAL for a negative or
+ * non-finite skin. */
+sevennet_status sevennet_md_set_skin(sevennet_md* md, double skin_A);
+/* Nose-Hoover NVT (Sec. 4 runs NVT; the paper gives no thermostat settings):
+ * one thermostat, dv/dt = F/m - xi v, dxi/dt = (2 K - N_f k_B T0) / Q,
+ * deta/dt = xi, N_f = 3N - 3, Q = N_f k_B T0 tau^2; each step is
+ * thermostat(dt/2), velocity Verlet(dt), thermostat(dt/2).  tau_fs <= 0 turns
+ * the thermostat off (NVE).  xi and eta persist across calls, so a schedule
+ * (a melt-quench ramp) sets a new temperature between md_step calls.  EINVAL
+ * for non-finite arguments, temperature <= 0 with tau > 0, or fewer than two
+ * atoms. */
+sevennet_status sevennet_md_set_nose_hoover(sevennet_md* md, double temperature_K, double tau_fs);
+/* Thermostat state: xi (1/fs) and eta (dimensionless); the conserved extended
+ * energy is E_pot + E_kin + Q xi^2 / 2 + N_f k_B T0 eta.  Synchronises. */
+sevennet_status sevennet_md_get_nose_hoover(const sevennet_md* md, double* xi, double* eta);
+/* Neighbour-list builds so far (the initial evaluation counts as one) and the
+ * edge count of the last refreshed Verlet list (0 without a skin). */
+sevennet_status sevennet_md_get_stats(const sevennet_md* md, int64_t* n_builds, int64_t* n_edges);
 void sevennet_md_destroy(sevennet_md* md);
 
 /* Serving: continuous batching of independent structures.  Requests are

@@ -88,6 +88,10 @@ SIGNATURES = {
     "sevennet_md_create": (_I32, [_P, _I64, _IP, _D, _D, _D, _D, ctypes.c_int, ctypes.POINTER(_P)]),
     "sevennet_md_step": (_I32, [_P, _I64, ctypes.c_double, _D, _D]),
     "sevennet_md_get_state": (_I32, [_P, _D, _D, _D]),
+    "sevennet_md_set_skin": (_I32, [_P, ctypes.c_double]),
+    "sevennet_md_set_nose_hoover": (_I32, [_P, ctypes.c_double, ctypes.c_double]),
+    "sevennet_md_get_nose_hoover": (_I32, [_P, _D, _D]),
+    "sevennet_md_get_stats": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "sevennet_md_destroy": (None, [_P]),
     "sevennet_server_create": (_I32, [_P, ctypes.c_size_t, _I32, _I32, ctypes.c_int, ctypes.POINTER(_P)]),
     "sevennet_server_submit": (_I32, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),

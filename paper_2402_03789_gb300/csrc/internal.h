@@ -329,9 +329,19 @@ struct BatchHost {
 
 // Neighbour build for a batch; positions/species are device arrays in input
 // order.  Leaves ws->row_ptr/src/dst/shift/geom/rev and the internal order.
+// r_list > 0 builds the list for that cutoff instead of the model's r_c (the
+// Verlet list of MD with a skin).
 sevennet_status build_neighbors(sevennet_model* M, Workspace* ws, const BatchHost& b,
                                 const double* pos_dev, const int32_t* species_dev,
-                                cudaStream_t st, int64_t* n_edges_out);
+                                cudaStream_t st, int64_t* n_edges_out, double r_list = 0.0);
+
+// The edges of a stored Verlet list (CSR in the internal order of the build that
+// made it: row_ptr, src, shift) that are within the model's r_c at the current
+// positions (input order), kept in list order, into ws->row_ptr/src/dst/shift/
+// geom/rev.  One structure; the internal order and cell of that build stay valid.
+sevennet_status refresh_neighbors(sevennet_model* M, Workspace* ws, int64_t n_atoms, const double* pos_dev,
+                                  const int* list_row_ptr, const int* list_src, const int* list_shift,
+                                  cudaStream_t st, int64_t* n_edges_out);
 
 // Model evaluation on the internal order prepared by build_neighbors.
 sevennet_status run_model(sevennet_model* M, Workspace* ws, const BatchHost& b, int64_t n_edges,

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <condition_variable>
 #include <deque>
 #include <mutex>
@@ -19,6 +20,7 @@
 namespace sn {
 
 constexpr double ACC_CONV = 9.64853321e-3;   // (eV / A / amu) -> A / fs^2
+constexpr double KB_EV = 8.617333262e-5;      // eV / K
 
 __global__ void kick_drift_kernel(int64_t n, double dt, const double* __restrict__ inv_m,
                                   const double* __restrict__ f, double* __restrict__ v,
@@ -59,6 +61,55 @@ __global__ void energies_kernel(int64_t n, const double* __restrict__ inv_m, con
     }
 }
 
+// Half of the Nose-Hoover splitting over time h (one CTA, fixed reduction order):
+//   xi += h/2 G;  v *= exp(-xi h);  eta += xi h;  xi += h/2 G,
+// G = (2 K - N_f k_B T0) / Q, K the kinetic energy at the current velocities
+// (after the scaling K becomes s^2 K exactly).  nh = {xi, eta}.
+__global__ void nh_half_kernel(int64_t n, double h, const double* __restrict__ inv_m, double* __restrict__ v,
+                               double* __restrict__ nh, double nf_kt0, double q) {
+    __shared__ double red[1024];
+    __shared__ double scale;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double m = ACC_CONV / inv_m[i];
+        s += m * (v[i * 3] * v[i * 3] + v[i * 3 + 1] * v[i * 3 + 1] + v[i * 3 + 2] * v[i * 3 + 2]);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double k = 0.5 * red[0] / ACC_CONV;
+        double xi = nh[0] + 0.5 * h * (2.0 * k - nf_kt0) / q;
+        const double f = exp(-xi * h);
+        const double eta = nh[1] + xi * h;
+        xi += 0.5 * h * (2.0 * k * f * f - nf_kt0) / q;
+        nh[0] = xi;
+        nh[1] = eta;
+        scale = f;
+    }
+    __syncthreads();
+    const double f = scale;
+    for (int64_t i = threadIdx.x; i < n * 3; i += blockDim.x) v[i] *= f;
+}
+
+// Largest squared displacement since the list was built, as the bit pattern of
+// a non-negative double (ordered like the value).
+__global__ void max_disp_kernel(int64_t n, const double* __restrict__ pos, const double* __restrict__ ref,
+                                unsigned long long* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double d2 = 0.0;
+    if (i < n) {
+        const double dx = pos[i * 3] - ref[i * 3], dy = pos[i * 3 + 1] - ref[i * 3 + 1],
+                     dz = pos[i * 3 + 2] - ref[i * 3 + 2];
+        d2 = dx * dx + dy * dy + dz * dz;
+    }
+    for (int o = 16; o > 0; o >>= 1) d2 = fmax(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(d2));
+}
+
 }  // namespace sn
 
 using namespace sn;
@@ -74,7 +125,82 @@ struct sevennet_md {
     double *pos = nullptr, *vel = nullptr, *f = nullptr, *inv_m = nullptr, *ev = nullptr;
     double *ekin = nullptr, *epot = nullptr;
     int64_t log_cap = 0;
+    // Verlet list (skin > 0): CSR in the internal order of its build, positions then
+    double skin = 0.0;
+    int *l_row = nullptr, *l_src = nullptr, *l_shift = nullptr;
+    int64_t l_cap = 0;
+    double* ref = nullptr;
+    unsigned long long* dmax = nullptr;
+    unsigned long long* dmax_host = nullptr;
+    bool have_list = false;
+    // Nose-Hoover thermostat (tau > 0): {xi, eta} on the device
+    double nh_T0 = 0.0, nh_tau = 0.0;
+    double* nh = nullptr;
+    int64_t n_builds = 0, n_edges = 0;
 };
+
+// Forces at the current positions.  Without a skin: a full neighbour build and
+// evaluation.  With a skin: the stored Verlet list (cutoff r_c + skin) is rebuilt
+// when some atom has moved more than skin / 2 since its build, and otherwise
+// filtered to r < r_c at the current positions (no pair can have entered r_c).
+static sevennet_status md_evaluate(sevennet_md* md) {
+    sevennet_model* M = md->M;
+    if (md->skin <= 0.0) {
+        SN_TRY(eval_batch(M, md->ws, md->b, md->species, md->pos, md->prec, md->ev, md->f, md->ev + 1, md->st));
+        ++md->n_builds;
+        return SEVENNET_OK;
+    }
+    bool rebuild = !md->have_list;
+    if (!rebuild) {
+        SN_CUDA(cudaMemsetAsync(md->dmax, 0, sizeof(unsigned long long), md->st));
+        max_disp_kernel<<<(unsigned)((md->N + 255) / 256), 256, 0, md->st>>>(md->N, md->pos, md->ref, md->dmax);
+        SN_CUDA(cudaMemcpyAsync(md->dmax_host, md->dmax, sizeof(unsigned long long), cudaMemcpyDeviceToHost, md->st));
+        SN_CUDA(cudaStreamSynchronize(md->st));
+        double d2;
+        std::memcpy(&d2, md->dmax_host, sizeof(double));
+        rebuild = !(d2 <= 0.25 * md->skin * md->skin);
+    }
+    const int64_t N = md->N;
+    if (rebuild) {
+        int64_t EL = 0;
+        SN_TRY(build_neighbors(M, md->ws, md->b, md->pos, md->species, md->st, &EL, M->cfg.r_cut + md->skin));
+        if (EL > md->l_cap) {
+            cudaFree(md->l_src);
+            cudaFree(md->l_shift);
+            md->l_src = md->l_shift = nullptr;
+            md->l_cap = 0;
+            const int64_t cap = EL + EL / 4 + 1024;
+            if (cudaMalloc(&md->l_src, cap * sizeof(int)) || cudaMalloc(&md->l_shift, cap * 3 * sizeof(int))) {
+                cudaGetLastError();
+                set_error("cudaMalloc failed for the Verlet list");
+                return SEVENNET_ENOMEM;
+            }
+            md->l_cap = cap;
+        }
+        if (!md->l_row && cudaMalloc(&md->l_row, (N + 1) * sizeof(int))) {
+            cudaGetLastError();
+            set_error("cudaMalloc failed for the Verlet list");
+            return SEVENNET_ENOMEM;
+        }
+        SN_CUDA(cudaMemcpyAsync(md->l_row, md->ws->row_ptr, (N + 1) * sizeof(int), cudaMemcpyDeviceToDevice, md->st));
+        if (EL > 0) {
+            SN_CUDA(cudaMemcpyAsync(md->l_src, md->ws->src, EL * sizeof(int), cudaMemcpyDeviceToDevice, md->st));
+            SN_CUDA(cudaMemcpyAsync(md->l_shift, md->ws->shift, EL * 3 * sizeof(int), cudaMemcpyDeviceToDevice,
+                                    md->st));
+        }
+        SN_CUDA(cudaMemcpyAsync(md->ref, md->pos, N * 3 * sizeof(double), cudaMemcpyDeviceToDevice, md->st));
+        md->have_list = true;
+        ++md->n_builds;
+    }
+    int64_t E = 0;
+    SN_TRY(refresh_neighbors(M, md->ws, N, md->pos, md->l_row, md->l_src, md->l_shift, md->st, &E));
+    md->n_edges = E;
+    SN_TRY(run_model(M, md->ws, md->b, E, md->prec, md->ev, md->f, md->ev + 1, md->st));
+    SN_CUDA(cudaMemcpyAsync(md->ws->flags_host, md->ws->flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, md->st));
+    SN_CUDA(cudaStreamSynchronize(md->st));
+    SN_CHECK(md->ws->flags_host[2] == 0, SEVENNET_ECUDA, "internal error: reverse edge not found");
+    return SEVENNET_OK;
+}
 
 extern "C" {
 
@@ -90,6 +216,13 @@ void sevennet_md_destroy(sevennet_md* md) {
     cudaFree(md->ev);
     cudaFree(md->ekin);
     cudaFree(md->epot);
+    cudaFree(md->l_row);
+    cudaFree(md->l_src);
+    cudaFree(md->l_shift);
+    cudaFree(md->ref);
+    cudaFree(md->dmax);
+    cudaFree(md->nh);
+    if (md->dmax_host) cudaFreeHost(md->dmax_host);
     ws_free(md->ws);
     if (md->st) cudaStreamDestroy(md->st);
     delete md;
@@ -124,7 +257,9 @@ sevennet_status sevennet_md_create(sevennet_model* M, int64_t n_atoms, const int
     const size_t n3 = (size_t)n_atoms * 3 * sizeof(double);
     if (cudaMalloc(&md->species, n_atoms * sizeof(int32_t)) || cudaMalloc(&md->pos, n3) ||
         cudaMalloc(&md->vel, n3) || cudaMalloc(&md->f, n3) || cudaMalloc(&md->inv_m, n_atoms * sizeof(double)) ||
-        cudaMalloc(&md->ev, 16 * sizeof(double))) {
+        cudaMalloc(&md->ev, 16 * sizeof(double)) || cudaMalloc(&md->ref, n3) ||
+        cudaMalloc(&md->dmax, sizeof(unsigned long long)) || cudaMalloc(&md->nh, 2 * sizeof(double)) ||
+        cudaMallocHost(&md->dmax_host, sizeof(unsigned long long))) {
         cudaGetLastError();
         set_error("cudaMalloc failed for MD state");
         return fail(SEVENNET_ENOMEM);
@@ -135,8 +270,13 @@ sevennet_status sevennet_md_create(sevennet_model* M, int64_t n_atoms, const int
         set_error("copy of MD state failed");
         return fail(SEVENNET_ECUDA);
     }
+    if (cudaMemset(md->nh, 0, 2 * sizeof(double))) {
+        set_error("cudaMemset failed");
+        return fail(SEVENNET_ECUDA);
+    }
     sevennet_status s = eval_batch(M, md->ws, md->b, md->species, md->pos, prec, md->ev, md->f, md->ev + 1, md->st);
     if (s) return fail(s);
+    md->n_builds = 1;
     *out = md;
     return SEVENNET_OK;
 }
@@ -159,10 +299,15 @@ sevennet_status sevennet_md_step(sevennet_md* md, int64_t n_steps, double dt_fs,
     }
     const int64_t n3 = md->N * 3;
     const unsigned blocks = (unsigned)((n3 + 255) / 256);
+    const bool nvt = md->nh_tau > 0.0;
+    const double nf_kt0 = (3.0 * md->N - 3.0) * KB_EV * md->nh_T0;
+    const double q = nf_kt0 * md->nh_tau * md->nh_tau;
     for (int64_t k = 0; k < n_steps; ++k) {
+        if (nvt) nh_half_kernel<<<1, 1024, 0, md->st>>>(md->N, 0.5 * dt_fs, md->inv_m, md->vel, md->nh, nf_kt0, q);
         kick_drift_kernel<<<blocks, 256, 0, md->st>>>(md->N, dt_fs, md->inv_m, md->f, md->vel, md->pos);
-        SN_TRY(eval_batch(md->M, md->ws, md->b, md->species, md->pos, md->prec, md->ev, md->f, md->ev + 1, md->st));
+        SN_TRY(md_evaluate(md));
         kick_kernel<<<blocks, 256, 0, md->st>>>(md->N, dt_fs, md->inv_m, md->f, md->vel);
+        if (nvt) nh_half_kernel<<<1, 1024, 0, md->st>>>(md->N, 0.5 * dt_fs, md->inv_m, md->vel, md->nh, nf_kt0, q);
         energies_kernel<<<1, 1024, 0, md->st>>>(md->N, md->inv_m, md->vel, md->ev, md->ekin + k, md->epot + k);
     }
     SN_CUDA(cudaGetLastError());
@@ -182,6 +327,40 @@ sevennet_status sevennet_md_get_state(const sevennet_md* md, double* pos, double
     if (pos) SN_CUDA(cudaMemcpy(pos, md->pos, n3, cudaMemcpyDeviceToHost));
     if (vel) SN_CUDA(cudaMemcpy(vel, md->vel, n3, cudaMemcpyDeviceToHost));
     if (forces) SN_CUDA(cudaMemcpy(forces, md->f, n3, cudaMemcpyDeviceToHost));
+    return SEVENNET_OK;
+}
+
+sevennet_status sevennet_md_set_skin(sevennet_md* md, double skin_A) {
+    SN_CHECK(md && std::isfinite(skin_A) && skin_A >= 0.0, SEVENNET_EINVAL, "skin must be finite and >= 0");
+    md->skin = skin_A;
+    md->have_list = false;             // the next step builds a list for the new skin
+    return SEVENNET_OK;
+}
+
+sevennet_status sevennet_md_set_nose_hoover(sevennet_md* md, double temperature_K, double tau_fs) {
+    SN_CHECK(md && std::isfinite(temperature_K) && std::isfinite(tau_fs), SEVENNET_EINVAL, "bad argument");
+    SN_CHECK(tau_fs <= 0.0 || temperature_K > 0.0, SEVENNET_EINVAL, "target temperature must be > 0");
+    SN_CHECK(md->N >= 2, SEVENNET_EINVAL, "a thermostat needs at least two atoms");
+    md->nh_T0 = temperature_K;
+    md->nh_tau = tau_fs > 0.0 ? tau_fs : 0.0;
+    return SEVENNET_OK;
+}
+
+sevennet_status sevennet_md_get_nose_hoover(const sevennet_md* md, double* xi, double* eta) {
+    SN_CHECK(md, SEVENNET_EINVAL, "NULL md");
+    SN_ENTER(md->M->device);
+    double h[2];
+    SN_CUDA(cudaStreamSynchronize(md->st));
+    SN_CUDA(cudaMemcpy(h, md->nh, sizeof(h), cudaMemcpyDeviceToHost));
+    if (xi) *xi = h[0];
+    if (eta) *eta = h[1];
+    return SEVENNET_OK;
+}
+
+sevennet_status sevennet_md_get_stats(const sevennet_md* md, int64_t* n_builds, int64_t* n_edges) {
+    SN_CHECK(md, SEVENNET_EINVAL, "NULL md");
+    if (n_builds) *n_builds = md->n_builds;
+    if (n_edges) *n_edges = md->n_edges;
     return SEVENNET_OK;
 }
 

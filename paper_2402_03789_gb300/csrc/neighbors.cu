@@ -324,10 +324,10 @@ static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t -
 
 sevennet_status build_neighbors(sevennet_model* M, Workspace* ws, const BatchHost& b,
                                 const double* pos_dev, const int32_t* species_dev,
-                                cudaStream_t st, int64_t* n_edges_out) {
+                                cudaStream_t st, int64_t* n_edges_out, double r_list) {
     const int S = b.n_structs;
     const int64_t N = b.atom_off[S];
-    const double rc = M->cfg.r_cut;
+    const double rc = r_list > 0.0 ? r_list : M->cfg.r_cut;
     // per-structure bins
     std::vector<int> sdesc((size_t)S * SD, 0);
     std::vector<double> inv((size_t)S * 9);
@@ -396,6 +396,87 @@ sevennet_status build_neighbors(sevennet_model* M, Workspace* ws, const BatchHos
             N, rc * rc, (float)rc, ws->cap_edges, ws->sdesc, ws->cells, ws->struct_of, ws->bin_start, ws->pos_s,
             ws->q32, ws->frac_floor, ws->row_ptr, nullptr, ws->flags, ws->dst, ws->src, ws->shift, ws->geom);
     }
+    if (E > 0)
+        reverse_kernel<<<blocks_for(E, 256), 256, 0, st>>>(E, ws->row_ptr, ws->dst, ws->src, ws->shift,
+                                                          ws->rev, ws->flags);
+    SN_CUDA(cudaGetLastError());
+    *n_edges_out = E;
+    return SEVENNET_OK;
+}
+
+// ---------------------------------------------------------------- Verlet list refresh
+// Group of NGL lanes per receiver v over its stored list entries, in order:
+// d = p_w - p_v + shift cell at the current positions (input order through perm),
+// FP64; kept when |d| < r_c.  Count pass, then fill pass into the compact CSR.
+template <bool FILL>
+__global__ void __launch_bounds__(128)
+refresh_kernel(int64_t n, double rc2, int64_t cap, const int* __restrict__ perm, const double* __restrict__ pos,
+               const double* __restrict__ cell, const int* __restrict__ lrow, const int* __restrict__ lsrc,
+               const int* __restrict__ lshift, const int* __restrict__ row_ptr, int* __restrict__ counts,
+               int* __restrict__ dst, int* __restrict__ src, int* __restrict__ shift, float4* __restrict__ geom) {
+    const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / NGL;
+    if (v >= n) return;
+    const int j = threadIdx.x & (NGL - 1);
+    const int gsh = threadIdx.x & 31 & ~(NGL - 1);
+    const unsigned gmask = ((1u << NGL) - 1) << gsh;
+    const int64_t ov = perm[v];
+    const double pv[3] = {pos[ov * 3], pos[ov * 3 + 1], pos[ov * 3 + 2]};
+    int64_t e = FILL ? (int64_t)row_ptr[v] : 0;
+    const int k1 = lrow[v + 1];
+    for (int k0 = lrow[v]; k0 < k1; k0 += NGL) {
+        const int k = k0 + j;
+        bool hit = false;
+        double dd[3], r2 = 0.0;
+        int w = 0, s0 = 0, s1 = 0, s2 = 0;
+        if (k < k1) {
+            w = lsrc[k];
+            s0 = lshift[k * 3]; s1 = lshift[k * 3 + 1]; s2 = lshift[k * 3 + 2];
+            const int64_t ow = perm[w];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                dd[a] = pos[ow * 3 + a] - pv[a] + (s0 * cell[a] + s1 * cell[3 + a] + s2 * cell[6 + a]);
+            r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+            hit = r2 < rc2;
+        }
+        const unsigned mine = (__ballot_sync(gmask, hit) >> gsh) & ((1u << NGL) - 1);
+        if constexpr (FILL) {
+            if (hit) {
+                const int64_t slot = e + __popc(mine & ((1u << j) - 1));
+                if (slot < cap) {
+                    dst[slot] = (int)v;
+                    src[slot] = w;
+                    shift[slot * 3 + 0] = s0;
+                    shift[slot * 3 + 1] = s1;
+                    shift[slot * 3 + 2] = s2;
+                    geom[slot] = make_float4((float)dd[0], (float)dd[1], (float)dd[2], (float)sqrt(r2));
+                }
+            }
+        }
+        e += __popc(mine);
+    }
+    if constexpr (!FILL) {
+        if (j == 0) counts[v] = (int)e;
+    }
+}
+
+sevennet_status refresh_neighbors(sevennet_model* M, Workspace* ws, int64_t N, const double* pos_dev,
+                                  const int* list_row_ptr, const int* list_src, const int* list_shift,
+                                  cudaStream_t st, int64_t* n_edges_out) {
+    const double rc = M->cfg.r_cut;
+    SN_CUDA(cudaMemsetAsync(ws->flags, 0, 8 * sizeof(int), st));
+    if (N > 0)
+        refresh_kernel<false><<<blocks_for(N * NGL, 128), 128, 0, st>>>(
+            N, rc * rc, 0, ws->perm, pos_dev, ws->cells, list_row_ptr, list_src, list_shift, nullptr,
+            ws->row_cnt, nullptr, nullptr, nullptr, nullptr);
+    scan_kernel<<<1, 1024, 0, st>>>(ws->row_cnt, N, ws->row_ptr, ws->flags + 0);
+    SN_CUDA(cudaMemcpyAsync(ws->flags_host, ws->flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    SN_CUDA(cudaStreamSynchronize(st));
+    const int64_t E = ws->flags_host[0];
+    SN_CHECK(E <= ws->cap_edges, SEVENNET_ECUDA, "internal error: refreshed list exceeds the edge capacity");
+    if (N > 0)
+        refresh_kernel<true><<<blocks_for(N * NGL, 128), 128, 0, st>>>(
+            N, rc * rc, ws->cap_edges, ws->perm, pos_dev, ws->cells, list_row_ptr, list_src, list_shift,
+            ws->row_ptr, nullptr, ws->dst, ws->src, ws->shift, ws->geom);
     if (E > 0)
         reverse_kernel<<<blocks_for(E, 256), 256, 0, st>>>(E, ws->row_ptr, ws->dst, ws->src, ws->shift,
                                                           ws->rev, ws->flags);

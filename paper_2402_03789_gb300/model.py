@@ -211,7 +211,7 @@ class SevenNet:
 
 
 class MD:
-    """NVE velocity-Verlet MD on the device."""
+    """Velocity-Verlet MD on the device (NVE, or Nose-Hoover NVT), optional Verlet skin."""
 
     def __init__(self, model: SevenNet, pos, vel, species, masses, cell, precision="fp32"):
         self.model = model
@@ -232,6 +232,28 @@ class MD:
         ek = np.zeros(n_steps)
         L.check(self.lib.sevennet_md_step(self.handle, n_steps, dt_fs, L.dptr(ep), L.dptr(ek)))
         return ep, ek
+
+    def set_skin(self, skin_A: float):
+        """Reuse a Verlet list of cutoff r_c + skin (0: rebuild every step)."""
+        L.check(self.lib.sevennet_md_set_skin(self.handle, float(skin_A)))
+
+    def set_nose_hoover(self, temperature_K: float, tau_fs: float):
+        """Nose-Hoover NVT at temperature_K with time constant tau_fs (tau <= 0: NVE)."""
+        L.check(self.lib.sevennet_md_set_nose_hoover(self.handle, float(temperature_K), float(tau_fs)))
+
+    def nose_hoover(self):
+        """(xi, eta) of the thermostat."""
+        xi = ctypes.c_double()
+        eta = ctypes.c_double()
+        L.check(self.lib.sevennet_md_get_nose_hoover(self.handle, ctypes.byref(xi), ctypes.byref(eta)))
+        return xi.value, eta.value
+
+    def stats(self):
+        """(neighbour-list builds so far, edges of the last refreshed Verlet list)."""
+        nb = ctypes.c_int64()
+        ne = ctypes.c_int64()
+        L.check(self.lib.sevennet_md_get_stats(self.handle, ctypes.byref(nb), ctypes.byref(ne)))
+        return nb.value, ne.value
 
     def state(self):
         p = np.zeros((self.n, 3))
