@@ -219,6 +219,22 @@ sevennet_status sevennet_conv_forward_noalloc(sevennet_model* model, int32_t lay
 sevennet_status sevennet_conv_dims(const sevennet_model* model, int32_t layer,
                                    int32_t* x_dim, int32_t* m_dim);
 
+/* Single-process emulation of the paper's multi-GPU spatial decomposition
+ * (Sec. 3.1, Figure 3) on one GPU: the cell is cut into n_domains slabs along
+ * its first lattice vector; each domain evaluates its own atoms with ghost
+ * copies of the atoms within r_c of them, exchanging h after every block
+ * (forward) and dE/dh and the partial edge forces backwards through device
+ * buffers.  Same arguments and outputs as sevennet_eval_energy_forces_virial
+ * (all periodic); the result equals the single-domain evaluation up to FP
+ * summation order.  A check of the decomposition scheme, not a fast path: it
+ * builds the domain graphs on the host.  EINVAL for n_domains outside [1, 64]
+ * and as sevennet_eval_energy_forces_virial. */
+sevennet_status sevennet_eval_decomposed(sevennet_model* model, int64_t n_atoms,
+                                         const int32_t* species, const double* pos,
+                                         const double* cell, int32_t n_domains,
+                                         sevennet_precision prec, double* energy,
+                                         double* forces, double* virial);
+
 /* Molecular dynamics: velocity Verlet in FP64 on the device (NVE by default),
  * neighbour list rebuilt every step unless a skin is set.  masses: amu per
  * species [n_species]; vel A/fs.  Positions, velocities and forces stay on the

@@ -88,6 +88,7 @@ SIGNATURES = {
     "sevennet_md_create": (_I32, [_P, _I64, _IP, _D, _D, _D, _D, ctypes.c_int, ctypes.POINTER(_P)]),
     "sevennet_md_step": (_I32, [_P, _I64, ctypes.c_double, _D, _D]),
     "sevennet_md_get_state": (_I32, [_P, _D, _D, _D]),
+    "sevennet_eval_decomposed": (_I32, [_P, _I64, _IP, _D, _D, ctypes.c_int32, ctypes.c_int, _D, _D, _D]),
     "sevennet_md_set_skin": (_I32, [_P, ctypes.c_double]),
     "sevennet_md_set_nose_hoover": (_I32, [_P, ctypes.c_double, ctypes.c_double]),
     "sevennet_md_get_nose_hoover": (_I32, [_P, _D, _D]),

@@ -392,101 +392,135 @@ void ws_free(Workspace* ws) {
 }
 
 // ---------------------------------------------------------------- evaluation
+static void run_gemm(sevennet_model* M, const GemmBatch& g, sevennet_precision prec, cudaStream_t st) {
+    if (!g.n) return;
+    cudaEvent_t ev;
+    prof_begin(&M->prof, PF_LINEAR, st, &ev);
+    launch_gemm(g, prec, st);
+    prof_end(&M->prof, PF_LINEAR, st, ev, 1);
+    count_launches(1);
+}
+
+void model_embed(sevennet_model* M, Workspace* ws, int64_t N, cudaStream_t st) {
+    cudaEvent_t ev;
+    prof_begin(&M->prof, PF_OTHER, st, &ev);
+    launch_embed(M->embed, ws->species_s, N, M->cfg.mul[0], M->cfg.n_species, ws->h, st);
+    prof_end(&M->prof, PF_OTHER, st, ev, 1);
+    count_launches(1);
+}
+
+// Block t forward on all N atoms: x = Lin1(h), y = LinSC(h); m = conv(x);
+// y += Lin2(m); h = Gate(y).  x and y are kept for the adjoint.
+void model_layer_forward(sevennet_model* M, Workspace* ws, int t, int64_t N, int64_t E,
+                         sevennet_precision prec, cudaStream_t st) {
+    const LayerDev& L = M->layers[t];
+    Profiler* P = &M->prof;
+    cudaEvent_t ev;
+    float* x = ws->xs + (size_t)t * N * M->x_max;
+    float* y = ws->ys + (size_t)t * N * M->y_max;
+    GemmBatch g{};
+    for (int l = 0; l < 3; ++l) {
+        if (!L.in_mul[l]) continue;
+        g.p[g.n++] = GemmProb{ws->h, L.lin1[l], L.lin1h[l], x, N, 2 * l + 1, L.in_mul[l], L.in_mul[l],
+                              L.h_in_dim, L.in_off[l], L.x_dim, L.in_off[l], 0};
+        if (L.y_mul[l])
+            g.p[g.n++] = GemmProb{ws->h, L.sc[l], L.sch[l], y, N, 2 * l + 1, L.in_mul[l], L.y_mul[l],
+                                  L.h_in_dim, L.in_off[l], L.y_dim, L.y_off[l], 0};
+    }
+    run_gemm(M, g, prec, st);
+    prof_begin(P, PF_CONV_FWD, st, &ev);
+    launch_conv_fwd(L, M->H, prec, N, E, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m, st);
+    prof_end(P, PF_CONV_FWD, st, ev, 1);
+    count_launches(1);
+    GemmBatch g2{};
+    for (int l = 0; l < 3; ++l) {
+        if (!L.y_mul[l] || !L.msg_mul[l]) continue;
+        g2.p[g2.n++] = GemmProb{ws->m, L.lin2[l], L.lin2h[l], y, N, 2 * l + 1, L.msg_mul[l], L.y_mul[l],
+                                L.m_dim, L.msg_off[l], L.y_dim, L.y_off[l], L.in_mul[l] ? 1 : 0};
+    }
+    run_gemm(M, g2, prec, st);
+    prof_begin(P, PF_GATE, st, &ev);
+    launch_gate_fwd(L, M->cfg.mul[0], M->cfg.mul, M->lmax, N, y, ws->h, st);
+    prof_end(P, PF_GATE, st, ev, 1);
+    count_launches(1);
+}
+
+void model_readout(sevennet_model* M, Workspace* ws, int64_t N, cudaStream_t st) {
+    cudaEvent_t ev;
+    const int mul0 = M->cfg.mul[0];
+    prof_begin(&M->prof, PF_OTHER, st, &ev);
+    launch_readout(ws->h, M->layers[M->T - 1].h_out_dim, M->readout, M->shift_dev, ws->species_s, N, mul0,
+                   M->cfg.n_species, ws->e_atom, st);
+    prof_end(&M->prof, PF_OTHER, st, ev, 1);
+    count_launches(1);
+}
+
+// Adjoint of the gate of block t: gy from gh (the last block takes the readout).
+void model_layer_backward_gate(sevennet_model* M, Workspace* ws, int t, int64_t N, cudaStream_t st) {
+    const LayerDev& L = M->layers[t];
+    cudaEvent_t ev;
+    float* y = ws->ys + (size_t)t * N * M->y_max;
+    prof_begin(&M->prof, PF_GATE, st, &ev);
+    launch_gate_bwd(L, M->cfg.mul[0], M->cfg.mul, M->lmax, N, y, ws->gh, M->readout, ws->gy, st);
+    prof_end(&M->prof, PF_GATE, st, ev, 1);
+    count_launches(1);
+}
+
+// The rest of the adjoint of block t: gm = Lin2^T(gy); conv adjoint (gx, and
+// dE/dd accumulated into gd); for t > 0 gh = Lin1^T(gx) + LinSC^T(gy).
+sevennet_status model_layer_backward_rest(sevennet_model* M, Workspace* ws, int t, int64_t N, int64_t E,
+                                          sevennet_precision prec, cudaStream_t st) {
+    const LayerDev& L = M->layers[t];
+    cudaEvent_t ev;
+    float* x = ws->xs + (size_t)t * N * M->x_max;
+    GemmBatch g{};
+    for (int l = 0; l < 3; ++l) {
+        if (!L.y_mul[l] || !L.msg_mul[l]) continue;
+        g.p[g.n++] = GemmProb{ws->gy, L.lin2T[l], L.lin2Th[l], ws->m, N, 2 * l + 1, L.y_mul[l], L.msg_mul[l],
+                              L.y_dim, L.y_off[l], L.m_dim, L.msg_off[l], 0};
+    }
+    run_gemm(M, g, prec, st);
+    SN_CUDA(cudaMemsetAsync(ws->gx, 0, (size_t)N * L.x_dim * sizeof(float), st));
+    prof_begin(&M->prof, PF_CONV_BWD, st, &ev);
+    launch_conv_bwd(L, M->H, prec, N, E, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m, ws->gx,
+                    ws->gd, st);
+    prof_end(&M->prof, PF_CONV_BWD, st, ev, 1);
+    count_launches(1);
+    if (t == 0) return SEVENNET_OK;
+    GemmBatch a{}, c{};
+    for (int l = 0; l < 3; ++l) {
+        if (!L.in_mul[l]) continue;
+        a.p[a.n++] = GemmProb{ws->gx, L.lin1T[l], L.lin1Th[l], ws->gh, N, 2 * l + 1, L.in_mul[l], L.in_mul[l],
+                              L.x_dim, L.in_off[l], L.h_in_dim, L.in_off[l], 0};
+        if (L.y_mul[l])
+            c.p[c.n++] = GemmProb{ws->gy, L.scT[l], L.scTh[l], ws->gh, N, 2 * l + 1, L.y_mul[l], L.in_mul[l],
+                                  L.y_dim, L.y_off[l], L.h_in_dim, L.in_off[l], 1};
+    }
+    run_gemm(M, a, prec, st);
+    run_gemm(M, c, prec, st);
+    return SEVENNET_OK;
+}
+
 sevennet_status run_model(sevennet_model* M, Workspace* ws, const BatchHost& b, int64_t E,
                           sevennet_precision prec, double* energy_dev, double* forces_dev,
                           double* virial_dev, cudaStream_t st) {
     const int64_t N = b.atom_off[b.n_structs];
     const int T = M->T;
-    const int mul0 = M->cfg.mul[0];
-    Profiler* P = &M->prof;
     cudaEvent_t ev;
-    auto gemm = [&](const GemmBatch& g) {
-        if (!g.n) return;
-        prof_begin(P, PF_LINEAR, st, &ev);
-        launch_gemm(g, prec, st);
-        prof_end(P, PF_LINEAR, st, ev, 1);
-        count_launches(1);
-    };
-    prof_begin(P, PF_OTHER, st, &ev);
-    launch_embed(M->embed, ws->species_s, N, mul0, M->cfg.n_species, ws->h, st);
-    prof_end(P, PF_OTHER, st, ev, 1);
-    count_launches(1);
-    for (int t = 0; t < T; ++t) {
-        const LayerDev& L = M->layers[t];
-        float* x = ws->xs + (size_t)t * N * M->x_max;
-        float* y = ws->ys + (size_t)t * N * M->y_max;
-        GemmBatch g{};
-        for (int l = 0; l < 3; ++l) {
-            if (!L.in_mul[l]) continue;
-            g.p[g.n++] = GemmProb{ws->h, L.lin1[l], L.lin1h[l], x, N, 2 * l + 1, L.in_mul[l], L.in_mul[l],
-                                  L.h_in_dim, L.in_off[l], L.x_dim, L.in_off[l], 0};
-            if (L.y_mul[l])
-                g.p[g.n++] = GemmProb{ws->h, L.sc[l], L.sch[l], y, N, 2 * l + 1, L.in_mul[l], L.y_mul[l],
-                                      L.h_in_dim, L.in_off[l], L.y_dim, L.y_off[l], 0};
-        }
-        gemm(g);
-        prof_begin(P, PF_CONV_FWD, st, &ev);
-        launch_conv_fwd(L, M->H, prec, N, E, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m, st);
-        prof_end(P, PF_CONV_FWD, st, ev, 1);
-        count_launches(1);
-        GemmBatch g2{};
-        for (int l = 0; l < 3; ++l) {
-            if (!L.y_mul[l] || !L.msg_mul[l]) continue;
-            g2.p[g2.n++] = GemmProb{ws->m, L.lin2[l], L.lin2h[l], y, N, 2 * l + 1, L.msg_mul[l], L.y_mul[l],
-                                    L.m_dim, L.msg_off[l], L.y_dim, L.y_off[l], L.in_mul[l] ? 1 : 0};
-        }
-        gemm(g2);
-        prof_begin(P, PF_GATE, st, &ev);
-        launch_gate_fwd(L, mul0, M->cfg.mul, M->lmax, N, y, ws->h, st);
-        prof_end(P, PF_GATE, st, ev, 1);
-        count_launches(1);
-    }
-    prof_begin(P, PF_OTHER, st, &ev);
-    launch_readout(ws->h, M->layers[T - 1].h_out_dim, M->readout, M->shift_dev, ws->species_s, N, mul0,
-                   M->cfg.n_species, ws->e_atom, st);
-    prof_end(P, PF_OTHER, st, ev, 1);
-    count_launches(1);
+    model_embed(M, ws, N, st);
+    for (int t = 0; t < T; ++t) model_layer_forward(M, ws, t, N, E, prec, st);
+    model_readout(M, ws, N, st);
     // reverse path
     if (E > 0) SN_CUDA(cudaMemsetAsync(ws->gd, 0, (size_t)E * 3 * sizeof(float), st));
     for (int t = T - 1; t >= 0; --t) {
-        const LayerDev& L = M->layers[t];
-        float* x = ws->xs + (size_t)t * N * M->x_max;
-        float* y = ws->ys + (size_t)t * N * M->y_max;
-        prof_begin(P, PF_GATE, st, &ev);
-        launch_gate_bwd(L, mul0, M->cfg.mul, M->lmax, N, y, ws->gh, M->readout, ws->gy, st);
-        prof_end(P, PF_GATE, st, ev, 1);
-        count_launches(1);
-        GemmBatch g{};
-        for (int l = 0; l < 3; ++l) {
-            if (!L.y_mul[l] || !L.msg_mul[l]) continue;
-            g.p[g.n++] = GemmProb{ws->gy, L.lin2T[l], L.lin2Th[l], ws->m, N, 2 * l + 1, L.y_mul[l], L.msg_mul[l],
-                                  L.y_dim, L.y_off[l], L.m_dim, L.msg_off[l], 0};
-        }
-        gemm(g);
-        SN_CUDA(cudaMemsetAsync(ws->gx, 0, (size_t)N * L.x_dim * sizeof(float), st));
-        prof_begin(P, PF_CONV_BWD, st, &ev);
-        launch_conv_bwd(L, M->H, prec, N, E, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m, ws->gx,
-                        ws->gd, st);
-        prof_end(P, PF_CONV_BWD, st, ev, 1);
-        count_launches(1);
-        if (t == 0) break;
-        GemmBatch a{}, c{};
-        for (int l = 0; l < 3; ++l) {
-            if (!L.in_mul[l]) continue;
-            a.p[a.n++] = GemmProb{ws->gx, L.lin1T[l], L.lin1Th[l], ws->gh, N, 2 * l + 1, L.in_mul[l], L.in_mul[l],
-                                  L.x_dim, L.in_off[l], L.h_in_dim, L.in_off[l], 0};
-            if (L.y_mul[l])
-                c.p[c.n++] = GemmProb{ws->gy, L.scT[l], L.scTh[l], ws->gh, N, 2 * l + 1, L.y_mul[l], L.in_mul[l],
-                                      L.y_dim, L.y_off[l], L.h_in_dim, L.in_off[l], 1};
-        }
-        gemm(a);
-        gemm(c);
+        model_layer_backward_gate(M, ws, t, N, st);
+        SN_TRY(model_layer_backward_rest(M, ws, t, N, E, prec, st));
     }
-    prof_begin(P, PF_OTHER, st, &ev);
+    prof_begin(&M->prof, PF_OTHER, st, &ev);
     launch_forces(N, ws->row_ptr, ws->rev, ws->gd, ws->geom, ws->f_s, ws->w_atom, st);
     launch_reduce_structs(b.n_structs, ws->atom_off, ws->e_atom, ws->w_atom, energy_dev, virial_dev, st);
     launch_scatter_forces(N, ws->perm, ws->f_s, forces_dev, st);
-    prof_end(P, PF_OTHER, st, ev, 3);
+    prof_end(&M->prof, PF_OTHER, st, ev, 3);
     count_launches(3);
     SN_CUDA(cudaGetLastError());
     return SEVENNET_OK;

@@ -343,6 +343,17 @@ sevennet_status refresh_neighbors(sevennet_model* M, Workspace* ws, int64_t n_at
                                   const int* list_row_ptr, const int* list_src, const int* list_shift,
                                   cudaStream_t st, int64_t* n_edges_out);
 
+// The steps of run_model, for drivers that interleave work between blocks
+// (the domain-decomposed evaluation): all operate on the N atoms and E edges of
+// the workspace's graph.
+void model_embed(sevennet_model* M, Workspace* ws, int64_t N, cudaStream_t st);
+void model_layer_forward(sevennet_model* M, Workspace* ws, int t, int64_t N, int64_t E,
+                         sevennet_precision prec, cudaStream_t st);
+void model_readout(sevennet_model* M, Workspace* ws, int64_t N, cudaStream_t st);
+void model_layer_backward_gate(sevennet_model* M, Workspace* ws, int t, int64_t N, cudaStream_t st);
+sevennet_status model_layer_backward_rest(sevennet_model* M, Workspace* ws, int t, int64_t N, int64_t E,
+                                          sevennet_precision prec, cudaStream_t st);
+
 // Model evaluation on the internal order prepared by build_neighbors.
 sevennet_status run_model(sevennet_model* M, Workspace* ws, const BatchHost& b, int64_t n_edges,
                           sevennet_precision prec, double* energy_dev, double* forces_dev,

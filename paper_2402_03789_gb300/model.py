@@ -107,6 +107,21 @@ class SevenNet:
             L.dptr(e), L.dptr(f), L.dptr(w)))
         return float(e[0]), f, w
 
+    def evaluate_decomposed(self, pos, cell, species, n_domains, precision="fp32"):
+        """(E, F, W) through the single-process emulation of the spatial
+        decomposition (n_domains slabs, ghost exchange per block)."""
+        pos = L.as_f64(pos, (-1, 3))
+        n = pos.shape[0]
+        sp = L.as_i32(species)
+        cell = L.as_f64(cell, (3, 3))
+        e = np.zeros(1)
+        f = np.zeros((n, 3))
+        w = np.zeros((3, 3))
+        L.check(self.lib.sevennet_eval_decomposed(self.handle, n, L.iptr(sp), L.dptr(pos), L.dptr(cell),
+                                                  int(n_domains), _prec(precision), L.dptr(e), L.dptr(f),
+                                                  L.dptr(w)))
+        return float(e[0]), f, w
+
     def neighbors(self, pos, cell, pbc=(1, 1, 1)):
         """Edges (dst, src, shift) with input atom indices, library order."""
         pos = L.as_f64(pos, (-1, 3))

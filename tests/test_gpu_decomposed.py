@@ -1,0 +1,57 @@
+"""Single-process emulation of the spatial decomposition (Sec. 3.1, Figure 3):
+the energy, forces and virial with the cell cut into 2-4 slab domains, each
+exchanging ghost features forward and gradients and partial forces backward
+after every block, equal the single-domain evaluation (and the oracle)."""
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import make_workload, normal_weights
+from gpu_common import errors, get_model
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n_domains", [1, 2, 3, 4])
+def test_decomposed_equals_single_domain_192(n_domains):
+    # 192-atom cell of 14.3 A: with 3-4 slabs a domain is thinner than r_c,
+    # so ghosts come from several domains and from periodic images
+    s, spec = make_workload("sio2_192_l2")
+    model = get_model(spec)
+    E1, F1, W1 = model.evaluate(s.pos, s.cell, s.species, "fp32")
+    E, F, W = model.evaluate_decomposed(s.pos, s.cell, s.species, n_domains, "fp32")
+    e_pa, f_rel, w_rel = errors(E, F, W, E1, F1, W1, s.n_atoms)
+    assert e_pa < 1e-8 and f_rel < 1e-6 and w_rel < 1e-6, (e_pa, f_rel, w_rel)
+
+
+def test_decomposed_matches_oracle_192():
+    s, spec = make_workload("sio2_192_l2")
+    model = get_model(spec)
+    w = normal_weights(oracle.n_params(spec))
+    Eo, Fo, Wo, *_ = oracle.energy_forces_virial(spec, w, s.species, s.pos, s.cell)
+    E, F, W = model.evaluate_decomposed(s.pos, s.cell, s.species, 3, "fp32")
+    e_pa, f_rel, w_rel = errors(E, F, W, Eo, Fo, Wo, s.n_atoms)
+    assert e_pa <= 1e-6 and f_rel <= 1e-5 and w_rel <= 1e-5, (e_pa, f_rel, w_rel)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_decomposed_equals_single_domain_3000(prec):
+    s, spec = make_workload("sio2_3000")
+    model = get_model(spec)
+    E1, F1, W1 = model.evaluate(s.pos, s.cell, s.species, prec)
+    E, F, W = model.evaluate_decomposed(s.pos, s.cell, s.species, 4, prec)
+    e_pa, f_rel, w_rel = errors(E, F, W, E1, F1, W1, s.n_atoms)
+    # the two evaluations differ only in FP32 summation order; in BF16 a last-bit
+    # difference can move a value across a BF16 rounding boundary of the hi/lo
+    # split (2^-16 relative), hence the wider bound there
+    tol = 1e-6 if prec == "fp32" else 1e-5
+    assert e_pa < 1e-8 and f_rel < tol and w_rel < tol, (e_pa, f_rel, w_rel)
+
+
+def test_decomposed_rejects_bad_domain_count():
+    import paper_2402_03789_gb300 as sn
+    s, spec = make_workload("sio2_192_l2")
+    model = get_model(spec)
+    with pytest.raises(sn.SevenNetError):
+        model.evaluate_decomposed(s.pos, s.cell, s.species, 0)
