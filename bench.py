@@ -301,6 +301,49 @@ def md_run(args, world, rank, dev, sn, model, s):
         print(json.dumps(line), flush=True)
 
 
+def paper_sweep(args, world, rank, dev, sn):
+    """The protocol of the paper's scaling benchmarks (Sec. 4) on one GPU:
+    NVT at 300 K (Nose-Hoover), 210 MD steps, wall time of the last 100, on
+    4,608 and 12,960 atoms of SiO2 at the alpha-quartz density, r_c 4 A,
+    2-5 layers, equal channels per irrep.  Supported here: lmax 2, 32 and 64
+    channels.  One JSON line per configuration and precision."""
+    import numpy as np
+    import torch
+    from synth import benchmark_model, make_quartz, maxwell_boltzmann, normal_weights
+    from synth.configs import MASSES_AMU
+    masses = np.asarray(MASSES_AMU)
+    for cell_name in ("quartz_4608", "quartz_12960"):
+        s = make_quartz(cell_name)
+        vel = maxwell_boltzmann(masses[s.species], 300.0, seed=12)
+        for n_layers in (2, 3, 4, 5):
+            for channels in (32, 64):
+                spec = benchmark_model(n_layers, channels)
+                model = sn.SevenNet(spec, normal_weights(sn.n_params(spec)), device=dev.index)
+                for prec in ("fp32", "bf16"):
+                    md = sn.MD(model, s.pos, vel, s.species, masses, s.cell, prec)
+                    md.set_nose_hoover(300.0, 100.0)
+                    md.step(110, 1.0)
+                    barrier(world)
+                    torch.cuda.synchronize(dev)
+                    t0 = time.perf_counter()
+                    md.step(100, 1.0)
+                    torch.cuda.synchronize(dev)
+                    wall = max_over_ranks(time.perf_counter() - t0, world, dev)
+                    md.close()
+                    line = {"metric": "atom-steps/s (NVT MD, paper benchmark protocol)",
+                            "value": world * s.n_atoms * 100 / wall, "unit": UNIT, "n_gpus": world,
+                            "steps": 100, "warmup": 110, "ms_per_step": wall * 10.0,
+                            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                            "dtype": "f32" if prec == "fp32" else "bf16+f32", "data": "synthetic",
+                            "config": {"workload": cell_name, "n_atoms": s.n_atoms, "n_layers": n_layers,
+                                       "channels": channels, "lmax": 2, "r_cut": 4.0, "precision": prec,
+                                       "ensemble": "NVT Nose-Hoover 300 K, tau 100 fs", "dt_fs": 1.0,
+                                       "parallelism": f"replicas x{world}"}}
+                    if rank == 0:
+                        print(json.dumps(line), flush=True)
+                model.close()
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -333,6 +376,8 @@ def main():
     ap.add_argument("--skin", type=float, default=0.0, help="MD: Verlet-list skin in A (0: rebuild every step)")
     ap.add_argument("--nvt", type=float, default=0.0, help="MD: Nose-Hoover target temperature in K (0: NVE)")
     ap.add_argument("--tau", type=float, default=100.0, help="MD: Nose-Hoover time constant in fs")
+    ap.add_argument("--paper-sweep", action="store_true",
+                    help="the paper's benchmark protocol (Sec. 4) over the supported model shapes")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -347,6 +392,9 @@ def main():
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    if args.paper_sweep:
+        paper_sweep(args, world, rank, dev, sn)
+        return
     s, spec = make_workload(args.workload)
     weights = normal_weights(sn.n_params(spec))
     model = sn.SevenNet(spec, weights, device=local)

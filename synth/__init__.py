@@ -9,10 +9,10 @@ library consume exactly the bytes produced here.
 
 from .configs import (  # noqa: F401
     SPECIES, SPECIES_Z, MASSES_AMU, ModelSpec, MODEL_TINY, MODEL_SEVENNET0,
-    MODEL_SEVENNET0_89, WEIGHT_SEED,
+    MODEL_SEVENNET0_89, WEIGHT_SEED, benchmark_model,
 )
 from .structures import (  # noqa: F401
     Structure, random_structure, cubic_length, WORKLOADS, make_workload,
-    serving_trace,
+    serving_trace, QUARTZ, make_quartz,
 )
 from .weights import normal_weights, maxwell_boltzmann  # noqa: F401

@@ -63,3 +63,14 @@ MODEL_SEVENNET0 = ModelSpec(n_species=3, n_layers=5, mul=(128, 64, 32),
 MODEL_SEVENNET0_89 = ModelSpec(n_species=89, n_layers=5, mul=(128, 64, 32),
                                r_cut=5.0, n_basis=8, poly_p=6, mlp_hidden=64,
                                avg_num_neigh=34.0, readout_hidden=64)
+
+
+# Shapes of the paper's scaling benchmarks (Sec. 4): channel counts 4-64 for
+# every irrep, 2-5 message-passing layers, lmax 3, cutoff 4.0 A, on alpha-quartz
+# SiO2.  Here lmax is at most 2 and channels are multiples of 32 (what the GPU
+# kernels are compiled for).  avg_num_neigh 21.4 is the mean neighbour count
+# within 4 A at 2.65 g/cm3 (4/3 pi r_c^3 x 0.0797 atoms/A^3), a normalisation
+# constant like SevenNet-0's.
+def benchmark_model(n_layers: int, channels: int, lmax: int = 2) -> "ModelSpec":
+    return ModelSpec(n_species=3, n_layers=n_layers, mul=(channels,) * (lmax + 1), r_cut=4.0,
+                     n_basis=8, poly_p=6, mlp_hidden=64, avg_num_neigh=21.4, readout_hidden=64)

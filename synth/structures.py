@@ -101,6 +101,21 @@ WORKLOADS = {
     "sio2_192_l2": ({"Si": 64, "O": 128}, 2.2, 1.6, 5, MODEL_SEVENNET0),
     "si3n4_112000": ({"Si": 48000, "N": 64000}, 3.1, 1.5, 7, MODEL_SEVENNET0),
 }
+
+# Stand-ins for the alpha-quartz cells of the paper's benchmarks (Sec. 4: 4,608
+# atoms per GPU in the scaled-size test, 12,960 atoms in the fixed-size test):
+# random SiO2 at the alpha-quartz density 2.65 g/cm3 (the trained models and
+# crystal snapshots are not available).  (counts, density, d_min, seed).
+QUARTZ = {
+    "quartz_216": ({"Si": 72, "O": 144}, 2.65, 1.6, 9),
+    "quartz_4608": ({"Si": 1536, "O": 3072}, 2.65, 1.6, 10),
+    "quartz_12960": ({"Si": 4320, "O": 8640}, 2.65, 1.6, 11),
+}
+
+
+def make_quartz(name: str):
+    counts, rho, dmin, seed = QUARTZ[name]
+    return random_structure(counts, rho, dmin, seed)
 VELOCITY_SEEDS = {"sio2_3000": 3, "si3n4_112000": 8}
 
 

@@ -1,0 +1,27 @@
+"""The shapes of the paper's scaling benchmarks (Sec. 4: r_c 4 A, equal
+channels for every irrep, 2-5 layers; lmax 2 here) against the FP64 oracle on
+a 216-atom cell at the alpha-quartz density, FP32 and BF16 paths."""
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import benchmark_model, make_quartz, normal_weights
+from gpu_common import errors, get_model
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n_layers,channels", [(2, 64), (5, 32), (3, 32)])
+def test_benchmark_shape_matches_oracle(n_layers, channels):
+    s = make_quartz("quartz_216")
+    spec = benchmark_model(n_layers, channels)
+    model = get_model(spec)
+    w = normal_weights(oracle.n_params(spec))
+    Eo, Fo, Wo, *_ = oracle.energy_forces_virial(spec, w, s.species, s.pos, s.cell)
+    E, F, W = model.evaluate(s.pos, s.cell, s.species, "fp32")
+    e_pa, f_rel, w_rel = errors(E, F, W, Eo, Fo, Wo, s.n_atoms)
+    assert e_pa <= 1e-6 and f_rel <= 1e-5 and w_rel <= 1e-5, (e_pa, f_rel, w_rel)
+    E, F, W = model.evaluate(s.pos, s.cell, s.species, "bf16")
+    e_pa, f_rel, w_rel = errors(E, F, W, Eo, Fo, Wo, s.n_atoms)
+    assert f_rel <= 5e-3, (e_pa, f_rel, w_rel)
