@@ -44,8 +44,20 @@ def real_sh(lmax: int, vec: torch.Tensor) -> list:
             s15 * x * z,
             0.5 * s15 * (x * x - y * y),
         ], dim=-1))
-    if lmax > 2:
-        raise NotImplementedError("real_sh: lmax <= 2")
+    if lmax >= 3:
+        # the standard real harmonics of degree 3 times sqrt(4 pi), m = -3..3
+        a, b, c, d = math.sqrt(70.0) / 4.0, math.sqrt(105.0), math.sqrt(42.0) / 4.0, math.sqrt(7.0) / 2.0
+        out.append(torch.stack([
+            a * y * (3.0 * x * x - y * y),
+            b * x * y * z,
+            c * y * (5.0 * z * z - 1.0),
+            d * z * (5.0 * z * z - 3.0),
+            c * x * (5.0 * z * z - 1.0),
+            0.5 * b * z * (x * x - y * y),
+            a * x * (x * x - 3.0 * y * y),
+        ], dim=-1))
+    if lmax > 3:
+        raise NotImplementedError("real_sh: lmax <= 3")
     return out
 
 

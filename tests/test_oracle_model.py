@@ -208,3 +208,26 @@ def test_five_layer_model_gradients_and_rotation():
     p[i, a] -= 2 * h
     Em = efv(spec, w, s, pos=p)[0]
     assert abs(-(Ep - Em) / (2 * h) - F[i, a]) <= 1e-6 * np.abs(F).max()
+
+
+def test_lmax3_model_invariances_and_forces():
+    # the paper's benchmark models have lmax 3 (Sec. 4): rotation and translation
+    # invariance, zero net force and central differences of the forces
+    from synth import benchmark_model, make_quartz
+    spec = benchmark_model(2, 32, lmax=3)
+    s = make_quartz("quartz_216")
+    w = normal_weights(oracle.n_params(spec))
+    E, F, W, *_ = efv(spec, w, s)
+    R = Rotation.random(random_state=3).as_matrix()
+    E2, F2, *_ = efv(spec, w, s, pos=s.pos @ R.T, cell=s.cell @ R.T)
+    assert abs(E2 - E) < 1e-10 * max(1.0, abs(E))
+    assert np.abs(F2 - F @ R.T).max() < 1e-10
+    assert np.abs(F.sum(0)).max() < 1e-10
+    h = 1e-4
+    for i, a in ((3, 0), (50, 2)):
+        p = s.pos.copy(); p[i, a] += h
+        Ep = efv(spec, w, s, pos=p)[0]
+        p[i, a] -= 2 * h
+        Em = efv(spec, w, s, pos=p)[0]
+        fd = -(Ep - Em) / (2 * h)
+        assert abs(fd - F[i, a]) <= 1e-6 * max(1.0, abs(F[i, a])) + 1e-9, (fd, F[i, a])

@@ -17,8 +17,8 @@ from scipy.special import sph_harm_y
 
 from oracle.so3 import real_sh, real_cg
 
-PATHS = [(l1, l2, l3) for l1 in range(3) for l2 in range(3)
-         for l3 in range(abs(l1 - l2), min(l1 + l2, 2) + 1)]
+PATHS = [(l1, l2, l3) for l1 in range(4) for l2 in range(4)
+         for l3 in range(abs(l1 - l2), min(l1 + l2, 3) + 1)]
 
 
 def _pts(n, seed):
@@ -27,16 +27,16 @@ def _pts(n, seed):
 
 def _fit_D(R):
     a, b = _pts(300, 11), _pts(300, 12)
-    Ya = real_sh(2, torch.tensor(a))
-    Yr = real_sh(2, torch.tensor(a @ R.T))
+    Ya = real_sh(3, torch.tensor(a))
+    Yr = real_sh(3, torch.tensor(a @ R.T))
     Ds = []
-    for l in range(3):
+    for l in range(4):
         Dl, *_ = np.linalg.lstsq(Ya[l].numpy(), Yr[l].numpy(), rcond=None)
         Ds.append(Dl.T)
     # validate on other points: the fit must hold there too
-    Yb = real_sh(2, torch.tensor(b))
-    Ybr = real_sh(2, torch.tensor(b @ R.T))
-    for l in range(3):
+    Yb = real_sh(3, torch.tensor(b))
+    Ybr = real_sh(3, torch.tensor(b @ R.T))
+    for l in range(4):
         assert np.abs(Yb[l].numpy() @ Ds[l].T - Ybr[l].numpy()).max() < 1e-12
     return Ds
 
@@ -46,8 +46,8 @@ def test_sh_matches_scipy_textbook_real_form():
     u = p / np.linalg.norm(p, axis=1, keepdims=True)
     theta = np.arccos(np.clip(u[:, 2], -1, 1))
     phi = np.arctan2(u[:, 1], u[:, 0])
-    Y = real_sh(2, torch.tensor(p))
-    for l in range(3):
+    Y = real_sh(3, torch.tensor(p))
+    for l in range(4):
         ref = np.zeros((p.shape[0], 2 * l + 1))
         for m in range(-l, l + 1):
             c = sph_harm_y(l, abs(m), theta, phi)
@@ -63,9 +63,9 @@ def test_sh_matches_scipy_textbook_real_form():
 
 def test_sh_addition_theorem_and_scale_invariance():
     p = torch.tensor(_pts(50, 2))
-    Y = real_sh(2, p)
-    Y2 = real_sh(2, 3.7 * p)
-    for l in range(3):
+    Y = real_sh(3, p)
+    Y2 = real_sh(3, 3.7 * p)
+    for l in range(4):
         assert torch.allclose((Y[l] ** 2).sum(-1), torch.full((50,), 2.0 * l + 1, dtype=torch.float64), atol=1e-12)
         assert torch.allclose(Y[l], Y2[l], atol=1e-14)
 
@@ -100,7 +100,7 @@ def test_cg_equivariance(seed):
 
 
 def test_cg_special_cases():
-    for l in range(3):
+    for l in range(4):
         assert np.allclose(real_cg(0, l, l)[0], np.eye(2 * l + 1))
         assert np.allclose(real_cg(l, 0, l)[:, 0, :], np.eye(2 * l + 1))
     # 1 x 1 -> 0 is the dot product / sqrt(3)
@@ -112,11 +112,11 @@ def test_cg_special_cases():
     assert np.allclose(f, np.cross(a, b)[perm] / math.sqrt(2))
 
 
-@pytest.mark.parametrize("l1,l2", [(1, 1), (0, 2), (1, 0)])
+@pytest.mark.parametrize("l1,l2", [(1, 1), (0, 2), (1, 0), (1, 2), (2, 1), (0, 3)])
 def test_cg_projects_products_of_harmonics(l1, l2):
     # sum_ab C[a,b,c] Y_l1(u)_a Y_l2(u)_b is proportional to Y_{l1+l2}(u)_c
     p = torch.tensor(_pts(40, 5))
-    Y = real_sh(2, p)
+    Y = real_sh(3, p)
     C = real_cg(l1, l2, l1 + l2)
     f = np.einsum("abc,na,nb->nc", C, Y[l1].numpy(), Y[l2].numpy())
     ratio = f / Y[l1 + l2].numpy()
