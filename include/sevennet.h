@@ -96,14 +96,16 @@ typedef struct sevennet_nlist sevennet_nlist;     /* opaque, device-resident nei
 typedef struct sevennet_md sevennet_md;           /* opaque MD state, device-resident */
 typedef struct sevennet_server sevennet_server;   /* opaque serving loop */
 
-/* Model hyper-parameters (Sec. 5.1).  lmax is 1 or 2; every mul[l] (l <= lmax)
- * is a positive multiple of 32; n_basis <= 16; mlp_hidden is 32 or 64;
- * readout_hidden <= 128.  shift may be NULL (all zero); it is copied. */
+/* Model hyper-parameters (Sec. 5.1; lmax 3 for the benchmark models of
+ * Sec. 4).  lmax is 1, 2 or 3 (3 needs mlp_hidden 64); every mul[l]
+ * (l <= lmax) is a multiple of 32 in [32, 256], entries above lmax are
+ * ignored; n_basis <= 16; mlp_hidden is 32 or 64; readout_hidden <= 1024.
+ * shift may be NULL (all zero); it is copied. */
 typedef struct {
     int32_t n_species;
     int32_t n_layers;
     int32_t lmax;
-    int32_t mul[3];
+    int32_t mul[4];
     double  r_cut;
     int32_t n_basis;
     int32_t poly_p;

@@ -27,7 +27,7 @@ class ModelConfig(ctypes.Structure):
         ("n_species", ctypes.c_int32),
         ("n_layers", ctypes.c_int32),
         ("lmax", ctypes.c_int32),
-        ("mul", ctypes.c_int32 * 3),
+        ("mul", ctypes.c_int32 * 4),
         ("r_cut", ctypes.c_double),
         ("n_basis", ctypes.c_int32),
         ("poly_p", ctypes.c_int32),

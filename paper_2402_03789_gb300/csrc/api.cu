@@ -95,7 +95,8 @@ static bool config_valid(const sevennet_model_config* c, std::string* why) {
     if (!c) return fail("config is NULL");
     if (c->n_species < 1) return fail("n_species must be >= 1");
     if (c->n_layers < 1 || c->n_layers > 16) return fail("n_layers must be in [1, 16]");
-    if (c->lmax < 1 || c->lmax > MAX_LMAX) return fail("lmax must be 1 or 2");
+    if (c->lmax < 1 || c->lmax > MAX_LMAX) return fail("lmax must be 1, 2 or 3");
+    if (c->lmax == 3 && c->mlp_hidden != 64) return fail("lmax 3 models need mlp_hidden 64");
     for (int l = 0; l <= c->lmax; ++l)
         if (c->mul[l] < 32 || c->mul[l] % 32 || c->mul[l] > 256) return fail("mul[l] must be a multiple of 32 in [32, 256]");
     if (!(c->r_cut > 0) || !std::isfinite(c->r_cut)) return fail("r_cut must be positive");
@@ -107,15 +108,15 @@ static bool config_valid(const sevennet_model_config* c, std::string* why) {
     return true;
 }
 
-static void block_irreps(const sevennet_model_config* c, int t, int in_mul[3], int y_mul[3],
-                         int out_mul[3], std::vector<PathH>& paths, int msg_mul[3], bool* last) {
+static void block_irreps(const sevennet_model_config* c, int t, int in_mul[NL], int y_mul[NL],
+                         int out_mul[NL], std::vector<PathH>& paths, int msg_mul[NL], bool* last) {
     const int T = c->n_layers, lmax = c->lmax;
     *last = (t == T - 1);
-    for (int l = 0; l < 3; ++l) in_mul[l] = y_mul[l] = out_mul[l] = msg_mul[l] = 0;
+    for (int l = 0; l < NL; ++l) in_mul[l] = y_mul[l] = out_mul[l] = msg_mul[l] = 0;
     if (t == 0) in_mul[0] = c->mul[0];
     else for (int l = 0; l <= lmax; ++l) in_mul[l] = c->mul[l];
     paths.clear();
-    for (int l1 = 0; l1 <= 2; ++l1) {
+    for (int l1 = 0; l1 <= MAX_LMAX; ++l1) {
         if (!in_mul[l1]) continue;
         for (int l2 = 0; l2 <= lmax; ++l2)
             for (int l3 = std::abs(l1 - l2); l3 <= std::min(l1 + l2, lmax); ++l3) {
@@ -134,9 +135,9 @@ static void block_irreps(const sevennet_model_config* c, int t, int in_mul[3], i
     }
 }
 
-static void offsets(const int mul[3], int off[3], int* dim) {
+static void offsets(const int mul[NL], int off[NL], int* dim) {
     int o = 0;
-    for (int l = 0; l < 3; ++l) { off[l] = o; o += (2 * l + 1) * mul[l]; }
+    for (int l = 0; l < NL; ++l) { off[l] = o; o += (2 * l + 1) * mul[l]; }
     *dim = o;
 }
 
@@ -149,21 +150,21 @@ static std::vector<WEntry> weight_entries(const sevennet_model_config* c) {
     add("embed", c->n_species, c->mul[0]);
     const int H = c->mlp_hidden;
     for (int t = 0; t < c->n_layers; ++t) {
-        int in_mul[3], y_mul[3], out_mul[3], msg_mul[3];
+        int in_mul[NL], y_mul[NL], out_mul[NL], msg_mul[NL];
         std::vector<PathH> paths;
         bool last;
         block_irreps(c, t, in_mul, y_mul, out_mul, paths, msg_mul, &last);
         const std::string p = "L" + std::to_string(t) + ".";
-        for (int l = 0; l < 3; ++l)
+        for (int l = 0; l < NL; ++l)
             if (y_mul[l] && in_mul[l]) add(p + "sc." + std::to_string(l), in_mul[l], y_mul[l]);
-        for (int l = 0; l < 3; ++l)
+        for (int l = 0; l < NL; ++l)
             if (in_mul[l]) add(p + "lin1." + std::to_string(l), in_mul[l], in_mul[l]);
         int W = 0;
         for (auto& q : paths) W += q.mul;
         add(p + "mlp0", c->n_basis, H);
         add(p + "mlp1", H, H);
         add(p + "mlp2", H, W);
-        for (int l = 0; l < 3; ++l)
+        for (int l = 0; l < NL; ++l)
             if (y_mul[l] && msg_mul[l]) add(p + "lin2." + std::to_string(l), msg_mul[l], y_mul[l]);
     }
     add("readout0", c->mul[0], c->readout_hidden);
@@ -419,7 +420,7 @@ void model_layer_forward(sevennet_model* M, Workspace* ws, int t, int64_t N, int
     float* x = ws->xs + (size_t)t * N * M->x_max;
     float* y = ws->ys + (size_t)t * N * M->y_max;
     GemmBatch g{};
-    for (int l = 0; l < 3; ++l) {
+    for (int l = 0; l < NL; ++l) {
         if (!L.in_mul[l]) continue;
         g.p[g.n++] = GemmProb{ws->h, L.lin1[l], L.lin1h[l], x, N, 2 * l + 1, L.in_mul[l], L.in_mul[l],
                               L.h_in_dim, L.in_off[l], L.x_dim, L.in_off[l], 0};
@@ -433,7 +434,7 @@ void model_layer_forward(sevennet_model* M, Workspace* ws, int t, int64_t N, int
     prof_end(P, PF_CONV_FWD, st, ev, 1);
     count_launches(1);
     GemmBatch g2{};
-    for (int l = 0; l < 3; ++l) {
+    for (int l = 0; l < NL; ++l) {
         if (!L.y_mul[l] || !L.msg_mul[l]) continue;
         g2.p[g2.n++] = GemmProb{ws->m, L.lin2[l], L.lin2h[l], y, N, 2 * l + 1, L.msg_mul[l], L.y_mul[l],
                                 L.m_dim, L.msg_off[l], L.y_dim, L.y_off[l], L.in_mul[l] ? 1 : 0};
@@ -474,7 +475,7 @@ sevennet_status model_layer_backward_rest(sevennet_model* M, Workspace* ws, int 
     cudaEvent_t ev;
     float* x = ws->xs + (size_t)t * N * M->x_max;
     GemmBatch g{};
-    for (int l = 0; l < 3; ++l) {
+    for (int l = 0; l < NL; ++l) {
         if (!L.y_mul[l] || !L.msg_mul[l]) continue;
         g.p[g.n++] = GemmProb{ws->gy, L.lin2T[l], L.lin2Th[l], ws->m, N, 2 * l + 1, L.y_mul[l], L.msg_mul[l],
                               L.y_dim, L.y_off[l], L.m_dim, L.msg_off[l], 0};
@@ -488,7 +489,7 @@ sevennet_status model_layer_backward_rest(sevennet_model* M, Workspace* ws, int 
     count_launches(1);
     if (t == 0) return SEVENNET_OK;
     GemmBatch a{}, c{};
-    for (int l = 0; l < 3; ++l) {
+    for (int l = 0; l < NL; ++l) {
         if (!L.in_mul[l]) continue;
         a.p[a.n++] = GemmProb{ws->gx, L.lin1T[l], L.lin1Th[l], ws->gh, N, 2 * l + 1, L.in_mul[l], L.in_mul[l],
                               L.x_dim, L.in_off[l], L.h_in_dim, L.in_off[l], 0};
@@ -613,7 +614,7 @@ sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const do
         offsets(L.msg_mul, L.msg_off, &L.m_dim);
         offsets(L.out_mul, L.out_off, &L.h_out_dim);
         L.x_dim = L.h_in_dim;
-        for (int l = 0; l < 3; ++l)
+        for (int l = 0; l < NL; ++l)
             if (L.y_mul[l] && !L.in_mul[l] && !L.msg_mul[l]) {
                 set_error("block %d: gate input irrep %d has no producer", t);
                 return fail(SEVENNET_EINVAL);
@@ -628,8 +629,8 @@ sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const do
         D.n_paths = (int)paths.size();
         if (D.n_paths > MAX_PATHS) { set_error("too many paths"); return fail(SEVENNET_EINVAL); }
         int col = 0, goff = 0;
-        int ch[3] = {0, 0, 0};
-        for (int l = 0; l < 3; ++l) { D.pbeg[l] = D.pend[l] = 0; }
+        int ch[NL] = {};
+        for (int l = 0; l < NL; ++l) { D.pbeg[l] = D.pend[l] = 0; }
         for (int p = 0; p < D.n_paths; ++p) {
             const PathH& q = paths[p];
             PathDesc& P = D.paths[p];
@@ -646,7 +647,7 @@ sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const do
             ch[q.l3] += q.mul;
             goff += ((2 * q.l1 + 1) * (2 * q.l3 + 1) + 3) & ~3;   // 16-byte aligned G blocks
         }
-        for (int l = 0; l < 3; ++l) {
+        for (int l = 0; l < NL; ++l) {
             int b = -1, e = -1;
             for (int p = 0; p < D.n_paths; ++p)
                 if (D.paths[p].l1 == l) { if (b < 0) b = p; e = p + 1; }
@@ -657,7 +658,7 @@ sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const do
             if (L.in_mul[l]) D.l1max = l;
         }
         D.kind = (t == 0 ? 1 : 0) | (L.last ? 2 : 0);
-        for (int l1 = 0; l1 <= 2; ++l1) {          // the kernels rely on this order
+        for (int l1 = 0; l1 <= MAX_LMAX; ++l1) {          // the kernels rely on this order
             const PathList pl = path_list(l1, cfg->lmax, D.kind);
             const int pb = path_begin(l1, cfg->lmax, D.kind);
             for (int i = 0; i < pl.n; ++i)
@@ -672,6 +673,7 @@ sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const do
         D.H = H;
         D.n_basis = NB;
         D.lmax = cfg->lmax;
+        D.ys = std::max(9, (cfg->lmax + 1) * (cfg->lmax + 1));
         D.x_dim = L.x_dim;
         D.m_dim = L.m_dim;
         D.nG = goff;
@@ -685,7 +687,7 @@ sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const do
         // weights
         const std::string pre = "L" + std::to_string(t) + ".";
         sevennet_status s;
-        for (int l = 0; l < 3; ++l) {
+        for (int l = 0; l < NL; ++l) {
             if (L.in_mul[l]) {
                 const WEntry* e = find(pre + "lin1." + std::to_string(l));
                 s = upload_linear(M, weights + e->off, e->rows, e->cols, 1.0 / std::sqrt((double)e->rows),

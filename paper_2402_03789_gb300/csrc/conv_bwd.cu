@@ -104,26 +104,28 @@ __device__ __forceinline__ void tp_bwd_chunk(const ConvDesc& D, int ne, const in
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int e = warp; e < ne; e += CONV_WARPS) {
         const int v = s_dst[e], sidx = s_src[e];
-        float gY[9];
+        constexpr int NYS = LMAX >= 3 ? 16 : 9;
+        float gY[NYS];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) gY[i] = 0.0f;
+        for (int i = 0; i < NYS; ++i) gY[i] = 0.0f;
         tp_bwd_l1<0, LMAX, KIND, MAXC>(D, lane, e, v, sidx, gY, s_w, s_G, x, gm, gx);
         tp_bwd_l1<1, LMAX, KIND, MAXC>(D, lane, e, v, sidx, gY, s_w, s_G, x, gm, gx);
         if constexpr (LMAX >= 2) tp_bwd_l1<2, LMAX, KIND, MAXC>(D, lane, e, v, sidx, gY, s_w, s_G, x, gm, gx);
+        if constexpr (LMAX >= 3) tp_bwd_l1<3, LMAX, KIND, MAXC>(D, lane, e, v, sidx, gY, s_w, s_G, x, gm, gx);
         constexpr int NY = (LMAX + 1) * (LMAX + 1);
 #pragma unroll
         for (int i = 0; i < NY; ++i) gY[i] = warp_sum(gY[i]);
-        if (lane < 9) {
+        if (lane < NYS) {
             float val = 0.0f;
 #pragma unroll
             for (int i = 0; i < NY; ++i) if (lane == i) val = gY[i];
-            s_gY[e * 9 + lane] = val;
+            s_gY[e * y_stride<LMAX>() + lane] = val;
         }
     }
 }
 
 template <int H, bool BF, int LMAX>
-__global__ void __launch_bounds__(CONV_THREADS, 2)
+__global__ void __launch_bounds__(CONV_THREADS, conv_ctas_per_sm(LMAX))
 conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __restrict__ W2,
                 const float* __restrict__ W2T, const float* __restrict__ W3, const float* __restrict__ W3T,
                 const __nv_bfloat16* __restrict__ W3T_h, const __nv_bfloat16* __restrict__ W3_h,
@@ -135,7 +137,7 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
                 float* __restrict__ gx, float* __restrict__ gd) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    const ConvSmem L = conv_smem_layout(D.Wpad, H, D.nG, true);
+    const ConvSmem L = conv_smem_layout(D.Wpad, H, D.nG, D.ys, true);
     __shared__ int s_range[2];
     cta_range(n_atoms, n_edges, row_ptr, s_range);
     const int v0 = s_range[0], v1 = s_range[1];
@@ -152,7 +154,7 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
     for (int c0 = E0; c0 < E1; c0 += EC) {
         const int ne = min(EC, E1 - c0);
         __syncthreads();
-        chunk_prologue<H, BF>(D, L, smem, c0, ne, pf, W2, W2T_h);
+        chunk_prologue<H, BF, LMAX>(D, L, smem, c0, ne, pf, W2, W2T_h);
         pf.fetch(c0 + EC, E1, dst, src, geom, row_ptr);   // next chunk's edges, in flight meanwhile
         // dE/dd of the blocks done so far, copied to shared memory for phase G
         if (t < 3 * ne) cp_async4(s_gdp + t, gd + (size_t)c0 * 3 + t);
@@ -256,13 +258,25 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
                 const float nc = 2.0f * c1 * cn - cm;
                 sm = sn; sn = ns; cm = cn; cn = nc;
             }
-            const float* gy = s_gY + t * 9;
+            const float* gy = s_gY + t * y_stride<LMAX>();
             const float s3 = 1.7320508075688772f, s15 = 3.872983346207417f, s5 = 2.23606797749979f;
             float gux = s3 * gy[3], guy = s3 * gy[1], guz = s3 * gy[2];
             if (D.lmax >= 2) {
                 gux += s15 * (uy * gy[4] + uz * gy[7] + ux * gy[8]);
                 guy += s15 * (ux * gy[4] + uz * gy[5] - uy * gy[8]);
                 guz += s15 * (uy * gy[5] + ux * gy[7]) + 3.0f * s5 * uz * gy[6];
+            }
+            if constexpr (LMAX >= 3) {   // gradients of the degree-3 polynomials (projected below)
+                const float a3 = 2.0916500663351889f, b3 = 10.246950765959598f;
+                const float c3 = 1.6201851746019651f, d3 = 1.3228756555322954f;
+                const float zz5 = 5.0f * uz * uz - 1.0f;
+                gux += gy[9] * 6.0f * a3 * ux * uy + gy[10] * b3 * uy * uz + gy[13] * c3 * zz5 +
+                       gy[14] * b3 * ux * uz + gy[15] * 3.0f * a3 * (ux * ux - uy * uy);
+                guy += gy[9] * 3.0f * a3 * (ux * ux - uy * uy) + gy[10] * b3 * ux * uz + gy[11] * c3 * zz5 -
+                       gy[14] * b3 * uy * uz - gy[15] * 6.0f * a3 * ux * uy;
+                guz += gy[10] * b3 * ux * uy + gy[11] * 10.0f * c3 * uy * uz +
+                       gy[12] * d3 * (15.0f * uz * uz - 3.0f) + gy[13] * 10.0f * c3 * ux * uz +
+                       gy[14] * 0.5f * b3 * (ux * ux - uy * uy);
             }
             const float dot = gux * ux + guy * uy + guz * uz;
             float* o = gd + (size_t)(c0 + t) * 3;
@@ -282,6 +296,8 @@ sevennet_status conv_configure_bwd(int H, size_t need) {
         SN_TRY(conv_set_smem((const void*)conv_bwd_kernel<64, true, 1>, need, &granted[hi][0]));
         SN_TRY(conv_set_smem((const void*)conv_bwd_kernel<64, false, 2>, need, &granted[hi][0]));
         SN_TRY(conv_set_smem((const void*)conv_bwd_kernel<64, true, 2>, need, &granted[hi][0]));
+        SN_TRY(conv_set_smem((const void*)conv_bwd_kernel<64, false, 3>, need, &granted[hi][1]));
+        SN_TRY(conv_set_smem((const void*)conv_bwd_kernel<64, true, 3>, need, &granted[hi][1]));
     } else if (H == 32) {
         SN_TRY(conv_set_smem((const void*)conv_bwd_kernel<32, false, 1>, need, &granted[hi][0]));
         SN_TRY(conv_set_smem((const void*)conv_bwd_kernel<32, true, 1>, need, &granted[hi][0]));
@@ -298,16 +314,16 @@ void launch_conv_bwd(const LayerDev& L, int H, sevennet_precision prec, int64_t 
                      int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
                      const float4* geom, const float* x, const float* gm, float* gx,
                      float* gd, cudaStream_t st) {
-    const int grid = conv_grid(n_atoms);
+    const int lm = L.conv.lmax;
+    const int grid = conv_grid(n_atoms, conv_ctas_per_sm(lm));
     const size_t sm = smem_bytes(L.conv, H, true);
     const bool bf = prec == SEVENNET_BF16;
 #define SN_LB(HH, BB, LL) conv_bwd_kernel<HH, BB, LL><<<grid, CONV_THREADS, sm, st>>>(                 \
         L.conv, L.mlp0, L.mlp1, L.mlp1T, L.mlp2, L.mlp2T, L.mlp2h, L.mlp2Th, L.mlp1Th, L.mlp1h,       \
         (int)n_atoms, (int)n_edges, row_ptr, dst, src, geom, x, gm, gx, gd)
-    const int lm = L.conv.lmax;
     if (H == 64) {
-        if (bf) { if (lm == 2) SN_LB(64, true, 2); else SN_LB(64, true, 1); }
-        else    { if (lm == 2) SN_LB(64, false, 2); else SN_LB(64, false, 1); }
+        if (bf) { if (lm == 3) SN_LB(64, true, 3); else if (lm == 2) SN_LB(64, true, 2); else SN_LB(64, true, 1); }
+        else    { if (lm == 3) SN_LB(64, false, 3); else if (lm == 2) SN_LB(64, false, 2); else SN_LB(64, false, 1); }
     } else {
         if (bf) { if (lm == 2) SN_LB(32, true, 2); else SN_LB(32, true, 1); }
         else    { if (lm == 2) SN_LB(32, false, 2); else SN_LB(32, false, 1); }

@@ -62,7 +62,7 @@ __device__ __forceinline__ void hk_inv(int i, int& k, int& e) {
     e = p & 15;
 }
 
-__host__ __device__ inline ConvSmem conv_smem_layout(int Wpad, int H, int nG, bool bwd) {
+__host__ __device__ inline ConvSmem conv_smem_layout(int Wpad, int H, int nG, int ys, bool bwd) {
     ConvSmem s;
     int o = 0;
     s.w = o;     o += EC * Wpad;
@@ -72,9 +72,9 @@ __host__ __device__ inline ConvSmem conv_smem_layout(int Wpad, int H, int nG, bo
     s.H2 = o;    o += H * EC;
     s.gH = o;    o += bwd ? H * EC : 0;
     s.G = o;     o += rup4(EC * nG);
-    s.Y = o;     o += EC * 9;
+    s.Y = o;     o += EC * ys;
     s.B = o;     o += MAX_NB * EC;
-    s.gY = o;    o += bwd ? EC * 9 : 0;
+    s.gY = o;    o += bwd ? EC * ys : 0;
     s.src = o;   o += EC;
     s.dst = o;   o += EC;
     s.first = o; o += EC;
@@ -110,6 +110,7 @@ __device__ __forceinline__ void envelope(const ConvDesc& D, float xr, float& u, 
 }
 
 // Phase A: Y_l(d/r) (component normalised, m = -l..l) and the enveloped basis.
+template <int LMAX>
 __device__ __forceinline__ void edge_features(const ConvDesc& D, float4 g, float* Y, float* Bcol,
                                               int bstride) {
     const float r = g.w;
@@ -127,6 +128,18 @@ __device__ __forceinline__ void edge_features(const ConvDesc& D, float4 g, float
     } else {
         Y[4] = Y[5] = Y[6] = Y[7] = Y[8] = 0.0f;
     }
+    if constexpr (LMAX >= 3) {   // degree 3 (m = -3..3), the standard real harmonics times sqrt(4 pi)
+        const float a3 = 2.0916500663351889f, b3 = 10.246950765959598f;    // sqrt(70)/4, sqrt(105)
+        const float c3 = 1.6201851746019651f, d3 = 1.3228756555322954f;    // sqrt(42)/4, sqrt(7)/2
+        const float zz5 = 5.0f * z * z;
+        Y[9] = a3 * y * (3.0f * x * x - y * y);
+        Y[10] = b3 * x * y * z;
+        Y[11] = c3 * y * (zz5 - 1.0f);
+        Y[12] = d3 * z * (zz5 - 3.0f);
+        Y[13] = c3 * x * (zz5 - 1.0f);
+        Y[14] = 0.5f * b3 * z * (x * x - y * y);
+        Y[15] = a3 * x * (x * x - 3.0f * y * y);
+    }
     float u, du;
     envelope(D, r / D.r_cut, u, du);
     const float th = 3.14159265358979f * r / D.r_cut;
@@ -143,15 +156,26 @@ __device__ __forceinline__ void edge_features(const ConvDesc& D, float4 g, float
 }
 
 // G matrices of one path for one edge.
+// Floats per edge of the Y and dE/dY tiles (also ConvDesc::ys).
+template <int LMAX>
+constexpr int y_stride() { return LMAX >= 3 ? 16 : 9; }
+
+// Only the couplings a kernel of degree LMAX can meet are compiled in.
+template <int LMAX>
 __device__ __forceinline__ void path_G(int kind, const float* Y, float* g) {
-    switch (kind) {
 #define SN_G(a, b, c) case coupling_kind(a, b, c): CG<a, b, c>::G(Y + (b) * (b), g); break;
-        SN_G(0, 0, 0) SN_G(0, 1, 1) SN_G(0, 2, 2)
-        SN_G(1, 0, 1) SN_G(1, 1, 0) SN_G(1, 1, 1) SN_G(1, 1, 2) SN_G(1, 2, 1) SN_G(1, 2, 2)
-        SN_G(2, 0, 2) SN_G(2, 1, 1) SN_G(2, 1, 2) SN_G(2, 2, 0) SN_G(2, 2, 1) SN_G(2, 2, 2)
-#undef SN_G
-        default: break;
+    if constexpr (LMAX <= 2) {
+        switch (kind) {
+            SN_FOR_EACH_COUPLING_L2(SN_G)
+            default: break;
+        }
+    } else {
+        switch (kind) {
+            SN_FOR_EACH_COUPLING(SN_G)
+            default: break;
+        }
     }
+#undef SN_G
 }
 
 // 4-byte asynchronous global -> shared copy (no register staging).
@@ -389,7 +413,7 @@ __device__ __forceinline__ void load_W1(const ConvDesc& D, const ConvSmem& L, fl
     for (int i = threadIdx.x; i < D.n_basis * H; i += CONV_THREADS) smem[L.W1 + i] = W1[i];
 }
 
-template <int H, bool BF>
+template <int H, bool BF, int LMAX>
 __device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem& L, float* smem,
                                                int c0, int ne, const EdgePrefetch& pf,
                                                const float* __restrict__ W2,
@@ -405,12 +429,12 @@ __device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem
             s_dst[t] = pf.dst;
             reinterpret_cast<int*>(smem + L.first)[t] = pf.first >= c0;   // receiver starts here
             reinterpret_cast<float4*>(smem + L.geo)[t] = pf.geom;
-            edge_features(D, pf.geom, s_Y + t * 9, s_B + t, EC);
+            edge_features<LMAX>(D, pf.geom, s_Y + t * y_stride<LMAX>(), s_B + t, EC);
         } else {
             s_src[t] = 0;
             s_dst[t] = -1;
             reinterpret_cast<float4*>(smem + L.geo)[t] = make_float4(0.f, 0.f, 0.f, 1.f);
-            for (int i = 0; i < 9; ++i) s_Y[t * 9 + i] = 0.0f;
+            for (int i = 0; i < y_stride<LMAX>(); ++i) s_Y[t * y_stride<LMAX>() + i] = 0.0f;
             for (int n = 0; n < D.n_basis; ++n) s_B[n * EC + t] = 0.0f;
         }
     }
@@ -446,7 +470,7 @@ __device__ __forceinline__ void chunk_prologue(const ConvDesc& D, const ConvSmem
     float* s_G = smem + L.G;
     for (int i = t; i < EC * D.n_paths; i += CONV_THREADS) {
         const int e = i % EC, p = i / EC;
-        path_G(D.paths[p].kind, s_Y + e * 9, s_G + e * D.nG + D.paths[p].g_off);
+        path_G<LMAX>(D.paths[p].kind, s_Y + e * y_stride<LMAX>(), s_G + e * D.nG + D.paths[p].g_off);
     }
     __syncthreads();
     if constexpr (BF) {          // A2 = H1 @ W2 on tensor cores, H2 = silu(A2)
@@ -657,13 +681,13 @@ __device__ __forceinline__ void chunk_gw_gemm_f32(const ConvDesc& D, const ConvS
 
 
 static inline size_t smem_bytes(const ConvDesc& D, int H, bool bwd) {
-    return (size_t)conv_smem_layout(D.Wpad, H, D.nG, bwd).total * sizeof(float);
+    return (size_t)conv_smem_layout(D.Wpad, H, D.nG, D.ys, bwd).total * sizeof(float);
 }
 
-static inline int conv_grid(int64_t n_atoms) {
+static inline int conv_grid(int64_t n_atoms, int ctas_per_sm) {
     int dev = 0;
     cudaGetDevice(&dev);
-    int g = 2 * num_sms(dev);                 // two CTAs per SM
+    int g = ctas_per_sm * num_sms(dev);
     if (n_atoms < g) g = (int)(n_atoms > 0 ? n_atoms : 1);
     return g;
 }

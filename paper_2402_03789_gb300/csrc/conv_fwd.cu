@@ -177,7 +177,7 @@ __device__ __forceinline__ void tp_fwd_chunk(const ConvDesc& D, int ne, const fl
 }
 
 template <int H, bool BF, int LMAX>
-__global__ void __launch_bounds__(CONV_THREADS, 2)
+__global__ void __launch_bounds__(CONV_THREADS, conv_ctas_per_sm(LMAX))
 conv_fwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __restrict__ W2,
                 const float* __restrict__ W3, const __nv_bfloat16* __restrict__ W3T_h,
                 const __nv_bfloat16* __restrict__ W2T_h, int n_atoms, int n_edges,
@@ -186,7 +186,7 @@ conv_fwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
                 const float* __restrict__ x, float* __restrict__ m) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    const ConvSmem L = conv_smem_layout(D.Wpad, H, D.nG, false);
+    const ConvSmem L = conv_smem_layout(D.Wpad, H, D.nG, D.ys, false);
     __shared__ int s_range[2];
     cta_range(n_atoms, n_edges, row_ptr, s_range);
     const int v0 = s_range[0], v1 = s_range[1];
@@ -207,7 +207,7 @@ conv_fwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
     for (int c0 = E0; c0 < E1; c0 += EC) {
         const int ne = min(EC, E1 - c0);
         __syncthreads();
-        chunk_prologue<H, BF>(D, L, smem, c0, ne, pf, W2, W2T_h);
+        chunk_prologue<H, BF, LMAX>(D, L, smem, c0, ne, pf, W2, W2T_h);
         pf.fetch(c0 + EC, E1, dst, src, geom, row_ptr);   // next chunk's edges, in flight meanwhile
         if constexpr (BF) chunk_w_gemm_bf16<H>(D, L, smem, W3T_h);
         else chunk_w_gemm_f32<H>(D, L, smem, W3);
@@ -244,18 +244,20 @@ void conv_prepare_edges(int64_t n_atoms, int64_t n_edges, const int* row_ptr, co
 size_t conv_smem_bytes(const ConvDesc& D, int H, bool bwd) { return smem_bytes(D, H, bwd); }
 
 sevennet_status conv_configure_fwd(int H, size_t need) {
-    static size_t granted[2] = {0, 0};
+    static size_t granted[2][2] = {{0, 0}, {0, 0}};
     const int hi = H == 64 ? 1 : 0;
     if (H == 64) {
-        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<64, false, 1>, need, &granted[hi]));
-        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<64, true, 1>, need, &granted[hi]));
-        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<64, false, 2>, need, &granted[hi]));
-        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<64, true, 2>, need, &granted[hi]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<64, false, 1>, need, &granted[hi][0]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<64, true, 1>, need, &granted[hi][0]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<64, false, 2>, need, &granted[hi][0]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<64, true, 2>, need, &granted[hi][0]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<64, false, 3>, need, &granted[hi][1]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<64, true, 3>, need, &granted[hi][1]));
     } else if (H == 32) {
-        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<32, false, 1>, need, &granted[hi]));
-        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<32, true, 1>, need, &granted[hi]));
-        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<32, false, 2>, need, &granted[hi]));
-        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<32, true, 2>, need, &granted[hi]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<32, false, 1>, need, &granted[hi][0]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<32, true, 1>, need, &granted[hi][0]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<32, false, 2>, need, &granted[hi][0]));
+        SN_TRY(conv_set_smem((const void*)conv_fwd_kernel<32, true, 2>, need, &granted[hi][0]));
     } else {
         set_error("radial MLP hidden width must be 32 or 64");
         return SEVENNET_EINVAL;
@@ -266,15 +268,15 @@ sevennet_status conv_configure_fwd(int H, size_t need) {
 void launch_conv_fwd(const LayerDev& L, int H, sevennet_precision prec, int64_t n_atoms,
                      int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
                      const float4* geom, const float* x, float* m, cudaStream_t st) {
-    const int grid = conv_grid(n_atoms);
+    const int lm = L.conv.lmax;
+    const int grid = conv_grid(n_atoms, conv_ctas_per_sm(lm));
     const size_t sm = smem_bytes(L.conv, H, false);
     const bool bf = prec == SEVENNET_BF16;
 #define SN_LF(HH, BB, LL) conv_fwd_kernel<HH, BB, LL><<<grid, CONV_THREADS, sm, st>>>(             \
         L.conv, L.mlp0, L.mlp1, L.mlp2, L.mlp2h, L.mlp1Th, (int)n_atoms, (int)n_edges, row_ptr, dst, src, geom, x, m)
-    const int lm = L.conv.lmax;
     if (H == 64) {
-        if (bf) { if (lm == 2) SN_LF(64, true, 2); else SN_LF(64, true, 1); }
-        else    { if (lm == 2) SN_LF(64, false, 2); else SN_LF(64, false, 1); }
+        if (bf) { if (lm == 3) SN_LF(64, true, 3); else if (lm == 2) SN_LF(64, true, 2); else SN_LF(64, true, 1); }
+        else    { if (lm == 3) SN_LF(64, false, 3); else if (lm == 2) SN_LF(64, false, 2); else SN_LF(64, false, 1); }
     } else {
         if (bf) { if (lm == 2) SN_LF(32, true, 2); else SN_LF(32, true, 1); }
         else    { if (lm == 2) SN_LF(32, false, 2); else SN_LF(32, false, 1); }

@@ -50,24 +50,31 @@ extern thread_local std::string g_last_error;
     } while (0)
 
 // ---------------------------------------------------------------- model
-constexpr int MAX_PATHS = 16;
+constexpr int MAX_PATHS = 40;
 constexpr int CONV_THREADS = 256;
 constexpr int CONV_WARPS = CONV_THREADS / 32;
 constexpr int MAX_SLOTS = 12;
 constexpr int EC = 16;                 // edges per chunk in the convolution kernels
+// CTAs per SM of the convolution kernels: two for lmax <= 2; the lmax 3 tiles
+// (34 paths) need more shared memory and registers than half an SM holds.
+__host__ __device__ constexpr int conv_ctas_per_sm(int lmax) { return lmax >= 3 ? 1 : 2; }
 constexpr int MAX_NB = 16;             // radial basis functions
-constexpr int MAX_LMAX = 2;
+constexpr int MAX_LMAX = 3;
+constexpr int NL = MAX_LMAX + 1;     // irreps l = 0..MAX_LMAX
 
-// kind = canonical index of the coupling (l1, l2, l3) among the 15 with l <= 2
+// kind = canonical index of the coupling (l1, l2, l3) among the 34 with l <= 3:
+// the 15 with every l <= 2 first (0..14, dense for the lmax <= 2 kernels), then
+// the 19 with some l = 3; within each group l1-major, then l2, then l3.
 __host__ __device__ constexpr int coupling_kind(int l1, int l2, int l3) {
-    // table order: l1-major, then l2, then l3 (matches the path order of a block)
     int k = 0;
-    for (int a = 0; a <= 2; ++a)
-        for (int b = 0; b <= 2; ++b)
-            for (int c = (a > b ? a - b : b - a); c <= (a + b < 2 ? a + b : 2); ++c) {
-                if (a == l1 && b == l2 && c == l3) return k;
-                ++k;
-            }
+    for (int top = 2; top <= MAX_LMAX; ++top)
+        for (int a = 0; a <= top; ++a)
+            for (int b = 0; b <= top; ++b)
+                for (int c = (a > b ? a - b : b - a); c <= (a + b < top ? a + b : top); ++c) {
+                    if (top > 2 && a <= 2 && b <= 2 && c <= 2) continue;     // counted in the first group
+                    if (a == l1 && b == l2 && c == l3) return k;
+                    ++k;
+                }
     return -1;
 }
 
@@ -77,12 +84,12 @@ __host__ __device__ constexpr int coupling_kind(int l1, int l2, int l3) {
 // the block's runtime path table.
 struct PathList {
     int n;
-    int l2[9];
-    int l3[9];
+    int l2[12];
+    int l3[12];
 };
 
 __host__ __device__ constexpr PathList path_list(int l1, int lmax, int kind) {
-    PathList p{0, {0, 0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0, 0, 0, 0}};
+    PathList p{0, {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}};
     if (((kind & 1) && l1 != 0) || l1 > lmax) return p;
     for (int l2 = 0; l2 <= lmax; ++l2)
         for (int l3 = (l1 > l2 ? l1 - l2 : l2 - l1); l3 <= (l1 + l2 < lmax ? l1 + l2 : lmax); ++l3) {
@@ -178,13 +185,14 @@ struct ConvDesc {
     int32_t H;          // hidden width of the radial MLP
     int32_t n_basis;
     int32_t lmax;       // spherical-harmonic degree
+    int32_t ys;         // floats per edge of the Y (and dE/dY) tiles: max(9, (lmax + 1)^2)
     int32_t x_dim;      // row width of x (block input after linear_1)
     int32_t m_dim;      // row width of the messages
     int32_t nG;         // floats of G per edge
     int32_t l1max;
-    int32_t mul_in[3];  // multiplicity of l in the block input (0 = absent)
-    int32_t x_off[3];
-    int32_t pbeg[3], pend[3];   // paths with l1 = l occupy [pbeg, pend)
+    int32_t mul_in[NL];  // multiplicity of l in the block input (0 = absent)
+    int32_t x_off[NL];
+    int32_t pbeg[NL], pend[NL];   // paths with l1 = l occupy [pbeg, pend)
     int32_t kind;               // bit 0: first block (input mul0 x 0e), bit 1: last block (l3 = 0)
     float r_cut;
     float env_a, env_b, env_c;  // envelope coefficients
@@ -216,8 +224,8 @@ struct GemmBatch {
 struct LayerDev {
     ConvDesc conv;
     int x_dim, y_dim, h_in_dim, h_out_dim, m_dim;
-    int in_mul[3], y_mul[3], msg_mul[3], out_mul[3];
-    int in_off[3], y_off[3], msg_off[3], out_off[3];
+    int in_mul[NL], y_mul[NL], msg_mul[NL], out_mul[NL];
+    int in_off[NL], y_off[NL], msg_off[NL], out_off[NL];
     bool last;
     // device weights, pre-scaled by 1/sqrt(fan_in) (and 1/avg_num_neigh for mlp2)
     float* mlp0 = nullptr;   // [NB][H]
@@ -230,9 +238,9 @@ struct LayerDev {
     __nv_bfloat16* mlp1Th = nullptr;  // [2][H][H] W2^T, hi then lo (B operand of H1 @ W2)
     __nv_bfloat16* mlp2h = nullptr;   // [W][H]  (N-major for mma B operand)
     __nv_bfloat16* mlp2Th = nullptr;  // [H][W]
-    float* lin1[3] = {};  float* lin1T[3] = {};  __nv_bfloat16* lin1h[3] = {};  __nv_bfloat16* lin1Th[3] = {};
-    float* sc[3] = {};    float* scT[3] = {};    __nv_bfloat16* sch[3] = {};    __nv_bfloat16* scTh[3] = {};
-    float* lin2[3] = {};  float* lin2T[3] = {};  __nv_bfloat16* lin2h[3] = {};  __nv_bfloat16* lin2Th[3] = {};
+    float* lin1[NL] = {};  float* lin1T[NL] = {};  __nv_bfloat16* lin1h[NL] = {};  __nv_bfloat16* lin1Th[NL] = {};
+    float* sc[NL] = {};    float* scT[NL] = {};    __nv_bfloat16* sch[NL] = {};    __nv_bfloat16* scTh[NL] = {};
+    float* lin2[NL] = {};  float* lin2T[NL] = {};  __nv_bfloat16* lin2h[NL] = {};  __nv_bfloat16* lin2Th[NL] = {};
 };
 
 struct Workspace;

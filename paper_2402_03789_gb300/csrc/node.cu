@@ -247,9 +247,15 @@ void launch_embed(const float* table, const int* species, int64_t n, int mul0, i
 // ---------------------------------------------------------------- gate
 struct GateDims {
     int mul0, ng, lmax, y_dim, h_dim;
-    int mul[3], y_off[3], h_off[3], goff[3];
+    int mul[NL], y_off[NL], h_off[NL], goff[NL];
     int last;
 };
+
+// Entry l (1..3) of a per-irrep array of the kernel parameter, by selects: a
+// dynamic index into a by-value parameter array would copy it to local memory.
+__device__ __forceinline__ int irrep_sel(const int (&a)[NL], int l) {
+    return l == 1 ? a[1] : (l == 2 ? a[2] : a[3]);
+}
 
 static GateDims gate_dims(const LayerDev& L, int mul0, const int* mul, int lmax) {
     GateDims g{};
@@ -259,7 +265,7 @@ static GateDims gate_dims(const LayerDev& L, int mul0, const int* mul, int lmax)
     g.h_dim = L.h_out_dim;
     g.last = L.last ? 1 : 0;
     int go = 0;
-    for (int l = 0; l <= 2; ++l) {
+    for (int l = 0; l < NL; ++l) {
         g.mul[l] = (l <= lmax) ? mul[l] : 0;
         g.y_off[l] = L.y_off[l];
         g.h_off[l] = L.out_off[l];
@@ -280,12 +286,11 @@ __global__ void gate_fwd_kernel(const GateDims G, int64_t n, const float* __rest
         h[i] = silu_(yr[j]);
         return;
     }
-    int l = 1;
-    if (G.lmax >= 2 && j >= G.h_off[2]) l = 2;
-    const int r = j - G.h_off[l];
-    const int u = r % G.mul[l];
-    const float gate = silu_(yr[G.mul0 + G.goff[l] + u]);
-    h[i] = yr[G.y_off[l] + r] * gate;
+    const int l = 1 + (G.lmax >= 2 && j >= G.h_off[2]) + (G.lmax >= 3 && j >= G.h_off[3]);
+    const int r = j - irrep_sel(G.h_off, l);
+    const int u = r % irrep_sel(G.mul, l);
+    const float gate = silu_(yr[G.mul0 + irrep_sel(G.goff, l) + u]);
+    h[i] = yr[irrep_sel(G.y_off, l) + r] * gate;
 }
 
 void launch_gate_fwd(const LayerDev& L, int mul0, const int* mul, int lmax, int64_t n,
@@ -316,21 +321,21 @@ __global__ void gate_bwd_kernel(const GateDims G, int64_t n, const float* __rest
     }
     if (j < G.mul0 + G.ng) {               // a gate scalar
         const int gidx = j - G.mul0;
-        const int l = (G.lmax >= 2 && gidx >= G.goff[2]) ? 2 : 1;
-        const int u = gidx - G.goff[l];
+        const int l = 1 + (G.lmax >= 2 && gidx >= G.goff[2]) + (G.lmax >= 3 && gidx >= G.goff[3]);
+        const int u = gidx - irrep_sel(G.goff, l);
+        const int ml = irrep_sel(G.mul, l), ho = irrep_sel(G.h_off, l), yo = irrep_sel(G.y_off, l);
         float s = 0.0f;
         for (int mm = 0; mm < 2 * l + 1; ++mm) {
-            const int off = mm * G.mul[l] + u;
-            s = fmaf(ghr[G.h_off[l] + off], yr[G.y_off[l] + off], s);
+            const int off = mm * ml + u;
+            s = fmaf(ghr[ho + off], yr[yo + off], s);
         }
         gy[i] = s * dsilu_(yr[j]);
         return;
     }
-    int l = 1;
-    if (G.lmax >= 2 && j >= G.y_off[2]) l = 2;
-    const int r = j - G.y_off[l];
-    const int u = r % G.mul[l];
-    gy[i] = ghr[G.h_off[l] + r] * silu_(yr[G.mul0 + G.goff[l] + u]);
+    const int l = 1 + (G.lmax >= 2 && j >= G.y_off[2]) + (G.lmax >= 3 && j >= G.y_off[3]);
+    const int r = j - irrep_sel(G.y_off, l);
+    const int u = r % irrep_sel(G.mul, l);
+    gy[i] = ghr[irrep_sel(G.h_off, l) + r] * silu_(yr[G.mul0 + irrep_sel(G.goff, l) + u]);
 }
 
 void launch_gate_bwd(const LayerDev& L, int mul0, const int* mul, int lmax, int64_t n,

@@ -22,7 +22,7 @@ def make_config(spec, shift=None):
     c.n_species = int(g("n_species"))
     c.n_layers = int(g("n_layers"))
     c.lmax = len(mul) - 1
-    for i in range(3):
+    for i in range(4):
         c.mul[i] = int(mul[i]) if i < len(mul) else 0
     c.r_cut = float(g("r_cut", 5.0))
     c.n_basis = int(g("n_basis", 8))

@@ -1,6 +1,7 @@
 """The shapes of the paper's scaling benchmarks (Sec. 4: r_c 4 A, equal
-channels for every irrep, 2-5 layers; lmax 2 here) against the FP64 oracle on
-a 216-atom cell at the alpha-quartz density, FP32 and BF16 paths."""
+channels for every irrep, 2-5 layers, lmax 2 and the paper's lmax 3) against
+the FP64 oracle on a 216-atom cell at the alpha-quartz density, FP32 and BF16
+paths."""
 
 import numpy as np
 import pytest
@@ -12,10 +13,10 @@ from gpu_common import errors, get_model
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("n_layers,channels", [(2, 64), (5, 32), (3, 32)])
-def test_benchmark_shape_matches_oracle(n_layers, channels):
+@pytest.mark.parametrize("n_layers,channels,lmax", [(2, 64, 2), (5, 32, 2), (3, 32, 2), (2, 32, 3), (3, 64, 3)])
+def test_benchmark_shape_matches_oracle(n_layers, channels, lmax):
     s = make_quartz("quartz_216")
-    spec = benchmark_model(n_layers, channels)
+    spec = benchmark_model(n_layers, channels, lmax=lmax)
     model = get_model(spec)
     w = normal_weights(oracle.n_params(spec))
     Eo, Fo, Wo, *_ = oracle.energy_forces_virial(spec, w, s.species, s.pos, s.cell)
