@@ -305,9 +305,9 @@ def paper_sweep(args, world, rank, dev, sn):
     """The protocol of the paper's scaling benchmarks (Sec. 4) on one GPU:
     NVT at 300 K (Nose-Hoover), 210 MD steps, wall time of the last 100, on
     4,608 and 12,960 atoms of SiO2 at the alpha-quartz density, r_c 4 A,
-    2-5 layers, equal channels per irrep, lmax 3 as in the paper and lmax 2.
-    Supported channel counts: 32 and 64.  One JSON line per configuration
-    and precision."""
+    2-5 layers, channels 4-64 per irrep (fewer than 32 run as the exact
+    zero-padded 32-channel model), lmax 3 as in the paper and lmax 2.  One
+    JSON line per configuration and precision."""
     import numpy as np
     import torch
     from synth import benchmark_model, make_quartz, maxwell_boltzmann, normal_weights
@@ -316,7 +316,7 @@ def paper_sweep(args, world, rank, dev, sn):
     for cell_name in ("quartz_4608", "quartz_12960"):
         s = make_quartz(cell_name)
         vel = maxwell_boltzmann(masses[s.species], 300.0, seed=12)
-        for lmax, n_layers, channels in [(l, n, c) for l in (3, 2) for n in (2, 3, 4, 5) for c in (32, 64)]:
+        for lmax, n_layers, channels in [(l, n, c) for l in (3, 2) for n in (2, 3, 4, 5) for c in (4, 8, 16, 32, 64)]:
             if True:
                 spec = benchmark_model(n_layers, channels, lmax=lmax)
                 model = sn.SevenNet(spec, normal_weights(sn.n_params(spec)), device=dev.index)

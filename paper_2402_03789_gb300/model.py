@@ -10,6 +10,7 @@ import ctypes
 import numpy as np
 
 from . import _lib as L
+from . import padding
 
 
 def make_config(spec, shift=None):
@@ -42,6 +43,8 @@ def make_config(spec, shift=None):
 
 
 def n_params(spec) -> int:
+    if not isinstance(spec, dict) and padding.needs_padding(spec):
+        return padding.n_params(spec)
     c, _keep = make_config(spec)
     n = L.load().sevennet_n_params(ctypes.byref(c))
     if n < 0:
@@ -70,6 +73,9 @@ class SevenNet:
 
     def __init__(self, spec, weights, device: int = 0):
         self.lib = L.load()
+        if not isinstance(spec, dict) and padding.needs_padding(spec):
+            # fewer than 32 channels of some irrep: the exact zero-padded model
+            spec, weights = padding.pad_model(spec, weights)
         cfg, keep = make_config(spec)
         self._cfg = cfg
         self._keep = keep

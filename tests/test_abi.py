@@ -5,6 +5,7 @@ every entry point declared in include/sevennet.h, and its host-only planning
 import os
 import re
 
+import numpy as np
 import pytest
 
 import oracle
@@ -45,7 +46,27 @@ def test_library_weight_layout_matches_oracle(lib, spec):
 
 def test_invalid_config_rejected(lib):
     import dataclasses
+    import ctypes
     import paper_2402_03789_gb300 as sn
-    bad = dataclasses.replace(MODEL_TINY, mul=(30, 32))
+    from paper_2402_03789_gb300.model import make_config
+    # the C ABI takes multiplicities that are multiples of 32 only (the Python
+    # binding pads smaller ones, exactly); a radial MLP width of 48 is invalid
+    c, _keep = make_config(dataclasses.replace(MODEL_TINY, mul=(30, 32)))
+    assert lib.sevennet_n_params(ctypes.byref(c)) < 0
     with pytest.raises(sn.SevenNetError):
-        sn.n_params(bad)
+        sn.n_params(dataclasses.replace(MODEL_TINY, mlp_hidden=48))
+
+
+def test_padding_walker_matches_oracle_layout():
+    # models with fewer than 32 channels run zero-padded: the binding's walk of
+    # the canonical weight layout must count exactly the oracle's parameters
+    import dataclasses
+    import oracle
+    from synth import MODEL_SEVENNET0, benchmark_model
+    from paper_2402_03789_gb300 import padding
+    for spec in (benchmark_model(3, 8, lmax=3), benchmark_model(2, 4), benchmark_model(5, 16, lmax=3),
+                 dataclasses.replace(MODEL_SEVENNET0, mul=(48, 16, 8))):
+        assert padding.n_params(spec) == oracle.n_params(spec)
+        spec_p, w_p = padding.pad_model(spec, np.arange(oracle.n_params(spec), dtype=np.float64))
+        assert all(m % 32 == 0 for m in spec_p.mul)
+        assert w_p.size == oracle.n_params(spec_p)

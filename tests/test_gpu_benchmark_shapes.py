@@ -26,3 +26,18 @@ def test_benchmark_shape_matches_oracle(n_layers, channels, lmax):
     E, F, W = model.evaluate(s.pos, s.cell, s.species, "bf16")
     e_pa, f_rel, w_rel = errors(E, F, W, Eo, Fo, Wo, s.n_atoms)
     assert f_rel <= 5e-3, (e_pa, f_rel, w_rel)
+
+
+@pytest.mark.parametrize("n_layers,channels,lmax", [(2, 4, 3), (3, 8, 3), (3, 16, 2)])
+def test_small_channel_models_match_oracle(n_layers, channels, lmax):
+    # the paper's 4-16 channel models run as the exact zero-padded 32-channel model
+    s = make_quartz("quartz_216")
+    spec = benchmark_model(n_layers, channels, lmax=lmax)
+    import paper_2402_03789_gb300 as sn
+    w = normal_weights(oracle.n_params(spec))
+    model = sn.SevenNet(spec, w)
+    Eo, Fo, Wo, *_ = oracle.energy_forces_virial(spec, w, s.species, s.pos, s.cell)
+    E, F, W = model.evaluate(s.pos, s.cell, s.species, "fp32")
+    e_pa, f_rel, w_rel = errors(E, F, W, Eo, Fo, Wo, s.n_atoms)
+    assert e_pa <= 1e-6 and f_rel <= 1e-5 and w_rel <= 1e-5, (e_pa, f_rel, w_rel)
+    model.close()
