@@ -209,17 +209,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// Activations enter the tensor cores as hi + lo BF16 pairs (two MMAs), weights as
-// one BF16 value: the product keeps ~16 mantissa bits of the activation.
-constexpr bool SPLIT_ACT = true;
-
-__device__ __forceinline__ void split_bf16(float x, float y, uint32_t& hi, uint32_t& lo) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
-    const float2 hf = __bfloat1622float2(h);
-    const __nv_bfloat162 l = __floats2bfloat162_rn(x - hf.x, y - hf.y);
-    hi = *reinterpret_cast<const uint32_t*>(&h);
-    lo = *reinterpret_cast<const uint32_t*>(&l);
-}
+// Activations enter the tensor cores as one BF16 value (round to nearest).  W3
+// is one BF16 value too; the hidden-layer weights W2 are a hi + lo BF16 pair
+// (two MMAs), which keeps the virial error of the BF16 path near that of its
+// forces (a single BF16 W2 raised it about fivefold).
 
 __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
     asm volatile(
@@ -247,14 +240,14 @@ __device__ __forceinline__ void chunk_w_gemm_bf16(const ConvDesc& D, const ConvS
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tq = lane & 3;
     const float* s_H2 = smem + L.H2;
     float* s_w = smem + L.w;
-    uint32_t af[KSN][4], al[KSN][4];
+    uint32_t af[KSN][4];
 #pragma unroll
     for (int ks = 0; ks < KSN; ++ks) {
         const int k0 = 2 * (tq * 2 * KSN + 2 * ks), k1 = k0 + 2;
-        split_bf16(s_H2[hk<H>(k0, g)], s_H2[hk<H>(k0 + 1, g)], af[ks][0], al[ks][0]);
-        split_bf16(s_H2[hk<H>(k0, g + 8)], s_H2[hk<H>(k0 + 1, g + 8)], af[ks][1], al[ks][1]);
-        split_bf16(s_H2[hk<H>(k1, g)], s_H2[hk<H>(k1 + 1, g)], af[ks][2], al[ks][2]);
-        split_bf16(s_H2[hk<H>(k1, g + 8)], s_H2[hk<H>(k1 + 1, g + 8)], af[ks][3], al[ks][3]);
+        af[ks][0] = pack_bf16(s_H2[hk<H>(k0, g)], s_H2[hk<H>(k0 + 1, g)]);
+        af[ks][1] = pack_bf16(s_H2[hk<H>(k0, g + 8)], s_H2[hk<H>(k0 + 1, g + 8)]);
+        af[ks][2] = pack_bf16(s_H2[hk<H>(k1, g)], s_H2[hk<H>(k1 + 1, g)]);
+        af[ks][3] = pack_bf16(s_H2[hk<H>(k1, g + 8)], s_H2[hk<H>(k1 + 1, g + 8)]);
     }
     const int ntiles = D.W / 8;
     for (int nb = warp; nb < ntiles; nb += BATCH * CONV_WARPS) {
@@ -278,7 +271,6 @@ __device__ __forceinline__ void chunk_w_gemm_bf16(const ConvDesc& D, const ConvS
             for (int ks = 0; ks < KSN; ++ks) {
                 const uint32_t b[2] = {bw[2 * ks], bw[2 * ks + 1]};
                 mma_bf16(c, af[ks], b);
-                if constexpr (SPLIT_ACT) mma_bf16(c, al[ks], b);
             }
             const int col = nt * 8 + 2 * tq;
             *reinterpret_cast<float2*>(s_w + g * D.Wpad + col) = make_float2(c[0], c[1]);
@@ -317,17 +309,13 @@ __device__ __forceinline__ void chunk_gw_gemm_bf16(const ConvDesc& D, const Conv
             const int c0 = kb * 32 + 8 * tq + 4 * ks;
             const float4 r0 = *reinterpret_cast<const float4*>(s_w + g * D.Wpad + c0);
             const float4 r1 = *reinterpret_cast<const float4*>(s_w + (g + 8) * D.Wpad + c0);
-            uint32_t a[4], al[4];
-            split_bf16(r0.x, r0.y, a[0], al[0]);
-            split_bf16(r1.x, r1.y, a[1], al[1]);
-            split_bf16(r0.z, r0.w, a[2], al[2]);
-            split_bf16(r1.z, r1.w, a[3], al[3]);
+            const uint32_t a[4] = {pack_bf16(r0.x, r0.y), pack_bf16(r1.x, r1.y), pack_bf16(r0.z, r0.w),
+                                   pack_bf16(r1.z, r1.w)};
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) {
                 const uint32_t* bw = reinterpret_cast<const uint32_t*>(&bv[nt]);
                 const uint32_t b[2] = {bw[2 * ks], bw[2 * ks + 1]};
                 mma_bf16(c[nt], a, b);
-                if constexpr (SPLIT_ACT) mma_bf16(c[nt], al, b);
             }
         }
     }
@@ -344,7 +332,7 @@ __device__ __forceinline__ void chunk_gw_gemm_bf16(const ConvDesc& D, const Conv
 
 // Hidden layer of the radial MLP on tensor cores (BF16 path):
 //   out[k_out][e] = sum_k in[k][e] B[k][k_out], B given N-major ([k_out][k]) as a
-//   hi + lo BF16 pair; three MMAs per k step (hi*hi, lo*hi, hi*lo).
+//   hi + lo BF16 pair, the input as one BF16 value; two MMAs per k step (in*hi, in*lo).
 // The 16 edges of the chunk are one m tile; warps take n tiles of 8 outputs.
 template <int H>
 struct HiddenB {                                   // B fragments of one n tile, hi and lo
@@ -374,15 +362,13 @@ __device__ __forceinline__ void hidden_mma(const float* __restrict__ s_in, const
 #pragma unroll
     for (int ks = 0; ks < KSN; ++ks) {
         const int k0 = 2 * (tq * 2 * KSN + 2 * ks), k1 = k0 + 2;
-        uint32_t a[4], al[4];
-        split_bf16(s_in[hk<H>(k0, g)], s_in[hk<H>(k0 + 1, g)], a[0], al[0]);
-        split_bf16(s_in[hk<H>(k0, g + 8)], s_in[hk<H>(k0 + 1, g + 8)], a[1], al[1]);
-        split_bf16(s_in[hk<H>(k1, g)], s_in[hk<H>(k1 + 1, g)], a[2], al[2]);
-        split_bf16(s_in[hk<H>(k1, g + 8)], s_in[hk<H>(k1 + 1, g + 8)], a[3], al[3]);
+        const uint32_t a[4] = {pack_bf16(s_in[hk<H>(k0, g)], s_in[hk<H>(k0 + 1, g)]),
+                               pack_bf16(s_in[hk<H>(k0, g + 8)], s_in[hk<H>(k0 + 1, g + 8)]),
+                               pack_bf16(s_in[hk<H>(k1, g)], s_in[hk<H>(k1 + 1, g)]),
+                               pack_bf16(s_in[hk<H>(k1, g + 8)], s_in[hk<H>(k1 + 1, g + 8)])};
         const uint32_t b[2] = {wh[2 * ks], wh[2 * ks + 1]};
         const uint32_t b2[2] = {wl[2 * ks], wl[2 * ks + 1]};
         mma_bf16(c, a, b);
-        if constexpr (SPLIT_ACT) mma_bf16(c, al, b);
         mma_bf16(c, a, b2);
     }
 }

@@ -42,10 +42,12 @@ def test_decomposed_equals_single_domain_3000(prec):
     E1, F1, W1 = model.evaluate(s.pos, s.cell, s.species, prec)
     E, F, W = model.evaluate_decomposed(s.pos, s.cell, s.species, 4, prec)
     e_pa, f_rel, w_rel = errors(E, F, W, E1, F1, W1, s.n_atoms)
-    # the two evaluations differ only in FP32 summation order; in BF16 a last-bit
-    # difference can move a value across a BF16 rounding boundary of the hi/lo
-    # split (2^-16 relative), hence the wider bound there
-    tol = 1e-6 if prec == "fp32" else 1e-5
+    # the two evaluations differ only in FP32 summation order.  In BF16 a last-bit
+    # difference can move a radial-MLP activation across a BF16 rounding boundary,
+    # which changes it by one BF16 ulp (2^-8 relative); the bound is a third of the
+    # BF16 path's own force error against the oracle (~1.5e-3), while the FP32 case
+    # pins the decomposition itself
+    tol = 1e-6 if prec == "fp32" else 5e-4
     assert e_pa < 1e-8 and f_rel < tol and w_rel < tol, (e_pa, f_rel, w_rel)
 
 

@@ -119,8 +119,12 @@ def test_batch_equals_alone(prec):
     e, f, w = model.evaluate_batch_dev(off, cells, sp, pos, prec)
     e, f, w = e.cpu().numpy(), f.cpu().numpy(), w.cpu().numpy()
     # equal up to FP32 summation order (chunk boundaries and adjoint atomics move
-    # with the batch), i.e. within the FP32 path's stated tolerances
+    # with the batch), i.e. within the FP32 path's stated tolerances.  In BF16 a
+    # last-bit difference can move a radial-MLP operand across a BF16 rounding
+    # boundary (one BF16 ulp, 2^-8 relative): there the bound is a third of the
+    # BF16 path's own force error against the oracle
+    tol = 1e-5 if prec == "fp32" else 5e-4
     for i, s in enumerate(structs):
         E1, F1, W1 = model.evaluate(s.pos, s.cell, s.species, prec)
         e_pa, f_rel, w_rel = errors(e[i], f[off[i]:off[i + 1]], w[i], E1, F1, W1, s.n_atoms)
-        assert e_pa <= 1e-6 and f_rel <= 1e-5 and w_rel <= 1e-5, (i, e_pa, f_rel, w_rel)
+        assert e_pa <= 1e-6 and f_rel <= tol and w_rel <= tol, (i, e_pa, f_rel, w_rel)
