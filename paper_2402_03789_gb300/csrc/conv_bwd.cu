@@ -137,7 +137,7 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
                 float* __restrict__ gx, float* __restrict__ gd) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    const ConvSmem L = conv_smem_layout(D.Wpad, H, D.nG, D.ys, true);
+    const ConvSmem L = conv_smem_layout(D.Wpad, H, D.nG, D.ys, true, BF);
     __shared__ int s_range[2];
     cta_range(n_atoms, n_edges, row_ptr, s_range);
     const int v0 = s_range[0], v1 = s_range[1];
@@ -316,7 +316,7 @@ void launch_conv_bwd(const LayerDev& L, int H, sevennet_precision prec, int64_t 
                      float* gd, cudaStream_t st) {
     const int lm = L.conv.lmax;
     const int grid = conv_grid(n_atoms, conv_ctas_per_sm(lm));
-    const size_t sm = smem_bytes(L.conv, H, true);
+    const size_t sm = smem_bytes(L.conv, H, true, prec == SEVENNET_BF16);
     const bool bf = prec == SEVENNET_BF16;
 #define SN_LB(HH, BB, LL) conv_bwd_kernel<HH, BB, LL><<<grid, CONV_THREADS, sm, st>>>(                 \
         L.conv, L.mlp0, L.mlp1, L.mlp1T, L.mlp2, L.mlp2T, L.mlp2h, L.mlp2Th, L.mlp1Th, L.mlp1h,       \

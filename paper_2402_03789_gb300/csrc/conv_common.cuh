@@ -62,15 +62,21 @@ __device__ __forceinline__ void hk_inv(int i, int& k, int& e) {
     e = p & 15;
 }
 
-__host__ __device__ inline ConvSmem conv_smem_layout(int Wpad, int H, int nG, int ys, bool bwd) {
+// The staging region holds H1 and dE/dbasis on both paths, and the W3 slices of
+// the FP32 phases D and F on the FP32 path only.  dE/dH2 (adjoint) reuses H2,
+// which is dead once phase D has run.  The BF16 kernels stay under 97 KB so two
+// CTAs leave about 60 KB of each SM's 256 KB to the L1 cache.
+__host__ __device__ inline ConvSmem conv_smem_layout(int Wpad, int H, int nG, int ys, bool bwd, bool bf) {
     ConvSmem s;
     int o = 0;
+    const int stage_bf = H * EC > MAX_NB * EC ? H * EC : MAX_NB * EC;
+    const int stage_f32 = KS * DCOLS > 2 * CS * 64 ? KS * DCOLS : 2 * CS * 64;
     s.w = o;     o += EC * Wpad;
-    s.stage = o; o += (KS * DCOLS > 2 * CS * 64 ? KS * DCOLS : 2 * CS * 64);
+    s.stage = o; o += bf ? stage_bf : (stage_f32 > stage_bf ? stage_f32 : stage_bf);
     s.A1 = o;    o += H * EC;
     s.A2 = o;    o += H * EC;
     s.H2 = o;    o += H * EC;
-    s.gH = o;    o += bwd ? H * EC : 0;
+    s.gH = s.H2;
     s.G = o;     o += rup4(EC * nG);
     s.Y = o;     o += EC * ys;
     s.B = o;     o += MAX_NB * EC;
@@ -666,8 +672,8 @@ __device__ __forceinline__ void chunk_gw_gemm_f32(const ConvDesc& D, const ConvS
 }
 
 
-static inline size_t smem_bytes(const ConvDesc& D, int H, bool bwd) {
-    return (size_t)conv_smem_layout(D.Wpad, H, D.nG, D.ys, bwd).total * sizeof(float);
+static inline size_t smem_bytes(const ConvDesc& D, int H, bool bwd, bool bf) {
+    return (size_t)conv_smem_layout(D.Wpad, H, D.nG, D.ys, bwd, bf).total * sizeof(float);
 }
 
 static inline int conv_grid(int64_t n_atoms, int ctas_per_sm) {

@@ -186,7 +186,7 @@ conv_fwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
                 const float* __restrict__ x, float* __restrict__ m) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    const ConvSmem L = conv_smem_layout(D.Wpad, H, D.nG, D.ys, false);
+    const ConvSmem L = conv_smem_layout(D.Wpad, H, D.nG, D.ys, false, BF);
     __shared__ int s_range[2];
     cta_range(n_atoms, n_edges, row_ptr, s_range);
     const int v0 = s_range[0], v1 = s_range[1];
@@ -241,7 +241,7 @@ void conv_prepare_edges(int64_t n_atoms, int64_t n_edges, const int* row_ptr, co
 }
 
 // ------------------------------------------------------------- launcher
-size_t conv_smem_bytes(const ConvDesc& D, int H, bool bwd) { return smem_bytes(D, H, bwd); }
+size_t conv_smem_bytes(const ConvDesc& D, int H, bool bwd) { return smem_bytes(D, H, bwd, false); }
 
 sevennet_status conv_configure_fwd(int H, size_t need) {
     static size_t granted[2][2] = {{0, 0}, {0, 0}};
@@ -270,7 +270,7 @@ void launch_conv_fwd(const LayerDev& L, int H, sevennet_precision prec, int64_t 
                      const float4* geom, const float* x, float* m, cudaStream_t st) {
     const int lm = L.conv.lmax;
     const int grid = conv_grid(n_atoms, conv_ctas_per_sm(lm));
-    const size_t sm = smem_bytes(L.conv, H, false);
+    const size_t sm = smem_bytes(L.conv, H, false, prec == SEVENNET_BF16);
     const bool bf = prec == SEVENNET_BF16;
 #define SN_LF(HH, BB, LL) conv_fwd_kernel<HH, BB, LL><<<grid, CONV_THREADS, sm, st>>>(             \
         L.conv, L.mlp0, L.mlp1, L.mlp2, L.mlp2h, L.mlp1Th, (int)n_atoms, (int)n_edges, row_ptr, dst, src, geom, x, m)
