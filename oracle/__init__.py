@@ -31,4 +31,4 @@ from .neighbors import neighbor_list_bruteforce, neighbor_list  # noqa: F401
 from .so3 import real_sh, real_cg  # noqa: F401
 from .radial import bessel_basis, poly_envelope  # noqa: F401
 from .md import (velocity_verlet, kinetic_energy, nose_hoover_q, nose_hoover_steps,  # noqa: F401
-                 nose_hoover_nvt)
+                 nose_hoover_nvt, ramp_target)

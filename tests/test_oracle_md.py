@@ -101,3 +101,53 @@ def test_nose_hoover_zero_forces_matches_ode():
         assert abs(out[3] - ref[1]) < 1e-3 * abs(ref[1]) + 1e-9
     assert errs[1] < 1e-4 * abs(ref[0]) + 1e-9
     assert 3.0 < errs[0] / errs[1] < 5.0, errs
+
+
+def test_nose_hoover_flat_ramp_equals_constant_target():
+    # a ramp from T to T is the constant-target thermostat, bit for bit
+    rng = np.random.default_rng(21)
+    n = 40
+    m = rng.uniform(10.0, 30.0, n)
+    v = maxwell_boltzmann(m, 800.0, seed=22)
+    pos = rng.uniform(0, 10, (n, 3))
+    spring = lambda p: (0.5 * float((p * p).sum()), -p)
+    a = oracle.nose_hoover_steps(spring, pos, v, m, 0.5, 30, 1200.0, 20.0)
+    b = oracle.nose_hoover_steps(spring, pos, v, m, 0.5, 30, 1200.0, 20.0, t_end_k=1200.0, ramp_steps=17)
+    for x, y in zip(a, b):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_ramp_target_midpoints():
+    # step k of an n-step ramp sits at the ramp's value at k + 1/2; afterwards the end value
+    vals = [oracle.ramp_target(3000.0, 2000.0, 4, k) for k in range(6)]
+    assert np.allclose(vals, [2875.0, 2625.0, 2375.0, 2125.0, 2000.0, 2000.0], rtol=0, atol=1e-12)
+    assert oracle.ramp_target(300.0, 5000.0, 0, 7) == 300.0
+
+
+def test_nose_hoover_ramp_zero_forces_matches_ode():
+    # F = 0 under a continuously ramped target T0(t) = T_s + (T_e - T_s) t / t_r and
+    # Q(t) = N_f k_B T0(t) tau^2: eta' = xi, xi' = (2 K0 exp(-2 eta) - N_f k_B T0(t)) / Q(t).
+    # The stepped schedule (target at each step's middle) converges to it at second order.
+    from scipy.integrate import solve_ivp
+    rng = np.random.default_rng(23)
+    n = 64
+    m = rng.uniform(10.0, 30.0, n)
+    v = maxwell_boltzmann(m, 1000.0, seed=24)
+    pos = rng.uniform(0, 10, (n, 3))
+    ts, te, tau, t_r = 1000.0, 3000.0, 10.0, 20.0
+    nf = 3 * n - 3
+    k0 = oracle.kinetic_energy(v, m)
+
+    def rhs(t, y):
+        t0 = ts + (te - ts) * t / t_r
+        return [y[1], (2.0 * k0 * np.exp(-2.0 * y[0]) - nf * KB * t0) / (nf * KB * t0 * tau * tau)]
+    ref = solve_ivp(rhs, (0.0, t_r), [0.0, 0.0], rtol=1e-12, atol=1e-14).y[:, -1]
+    zero = lambda p: (0.0, np.zeros_like(p))
+    errs = []
+    for dt in (0.2, 0.1):
+        steps = int(round(t_r / dt))
+        out = oracle.nose_hoover_steps(zero, pos, v, m, dt, steps, ts, tau, t_end_k=te, ramp_steps=steps)
+        errs.append(abs(out[4] - ref[0]))
+        assert abs(out[3] - ref[1]) < 1e-3 * abs(ref[1]) + 1e-9
+    assert errs[1] < 1e-4 * abs(ref[0]) + 1e-9
+    assert 3.0 < errs[0] / errs[1] < 5.0, errs
