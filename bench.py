@@ -301,6 +301,57 @@ def md_run(args, world, rank, dev, sn, model, s):
         print(json.dumps(line), flush=True)
 
 
+def melt_quench_run(args, world, rank, dev, sn, model, s):
+    """The melt-quench protocol of Sec. 5.2 under Nose-Hoover NVT, every
+    duration multiplied by args.melt_quench: hold at 5000 K for 10 ps, hold at
+    3000 K for 20 ps, quench to 2000 K at -33 K/ps (30.3 ps); dt = 1 fs.
+    atom-steps/s over the whole schedule and the temperature at the end of each
+    segment."""
+    import numpy as np
+    import torch
+    from synth import maxwell_boltzmann
+    from synth.configs import MASSES_AMU
+    masses = np.asarray(MASSES_AMU)
+    f = args.melt_quench
+    segs = [("hold", 5000.0, max(1, int(round(10000 * f)))),
+            ("hold", 3000.0, max(1, int(round(20000 * f)))),
+            ("ramp", 3000.0, 2000.0, max(1, int(round(1000.0 / 33.0 * 1000 * f))))]
+    vel = maxwell_boltzmann(masses[s.species], 5000.0, seed=MD_VEL_SEED.get(args.workload, 3))
+    md = sn.MD(model, s.pos, vel, s.species, masses, s.cell, args.precision)
+    if args.skin > 0:
+        md.set_skin(args.skin)
+    md.set_nose_hoover(5000.0, args.tau)
+    md.step(args.warmup, 1.0)
+    clk = ClockSampler(dev.index)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clk.start()
+    t0 = time.perf_counter()
+    ep, ek = md.run_schedule(segs, 1.0, args.tau)
+    torch.cuda.synchronize(dev)
+    wall = max_over_ranks(time.perf_counter() - t0, world, dev)
+    clk.stop()
+    n, steps = s.n_atoms, len(ep)
+    kb, nf = 8.617333262e-5, 3 * s.n_atoms - 3
+    ends = np.cumsum([sg[-1] for sg in segs]) - 1
+    line = {"metric": "atom-steps/s (NVT melt-quench schedule of Sec. 5.2, time-scaled)",
+            "value": world * n * steps / wall, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": wall * 1e3 / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16+f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n_atoms": n, "precision": args.precision, "dt_fs": 1.0,
+                       "time_scale": f, "schedule": [list(sg) for sg in segs], "tau_fs": args.tau,
+                       "skin_A": args.skin, "timing": "host wall clock around the schedule",
+                       "parallelism": f"replicas x{world}"},
+            "melt_quench": {"T_end_of_segment_K": [float(2 * ek[i] / (nf * kb)) for i in ends],
+                            "epot_final_eV_per_atom": float(ep[-1] / n),
+                            "finite": bool(np.all(np.isfinite(ep + ek)))},
+            "clocks": clk.summary()}
+    md.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def paper_sweep(args, world, rank, dev, sn):
     """The protocol of the paper's scaling benchmarks (Sec. 4) on one GPU:
     NVT at 300 K (Nose-Hoover), 210 MD steps, wall time of the last 100, on
@@ -377,6 +428,9 @@ def main():
     ap.add_argument("--skin", type=float, default=0.0, help="MD: Verlet-list skin in A (0: rebuild every step)")
     ap.add_argument("--nvt", type=float, default=0.0, help="MD: Nose-Hoover target temperature in K (0: NVE)")
     ap.add_argument("--tau", type=float, default=100.0, help="MD: Nose-Hoover time constant in fs")
+    ap.add_argument("--melt-quench", type=float, default=0.0,
+                    help="run the melt-quench schedule of Sec. 5.2 with every duration times this factor "
+                         "(default workload: the 112,000-atom Si3N4 cell)")
     ap.add_argument("--paper-sweep", action="store_true",
                     help="the paper's benchmark protocol (Sec. 4) over the supported model shapes")
     args = ap.parse_args()
@@ -396,11 +450,16 @@ def main():
     if args.paper_sweep:
         paper_sweep(args, world, rank, dev, sn)
         return
+    if args.melt_quench > 0 and args.workload == WORKLOAD:
+        args.workload = "si3n4_112000"
     s, spec = make_workload(args.workload)
     weights = normal_weights(sn.n_params(spec))
     model = sn.SevenNet(spec, weights, device=local)
     if args.md_steps > 0:
         md_run(args, world, rank, dev, sn, model, s)
+        return
+    if args.melt_quench > 0:
+        melt_quench_run(args, world, rank, dev, sn, model, s)
         return
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     species = torch.tensor(s.species, dtype=torch.int32, device=dev)

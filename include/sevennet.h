@@ -268,10 +268,20 @@ sevennet_status sevennet_md_set_skin(sevennet_md* md, double skin_A);
  * deta/dt = xi, N_f = 3N - 3, Q = N_f k_B T0 tau^2; each step is
  * thermostat(dt/2), velocity Verlet(dt), thermostat(dt/2).  tau_fs <= 0 turns
  * the thermostat off (NVE).  xi and eta persist across calls, so a schedule
- * (a melt-quench ramp) sets a new temperature between md_step calls.  EINVAL
+ * may set a new temperature between md_step calls.  EINVAL
  * for non-finite arguments, temperature <= 0 with tau > 0, or fewer than two
  * atoms. */
 sevennet_status sevennet_md_set_nose_hoover(sevennet_md* md, double temperature_K, double tau_fs);
+/* Nose-Hoover NVT whose target ramps linearly from t_start_K to t_end_K over
+ * the next n_steps steps (counted across md_step calls), then stays at
+ * t_end_K: the melt-quench schedule of Sec. 5.2 (hold at 5000 K, hold at
+ * 3000 K, quench at -33 K/ps) is a sequence of holds and ramps.  Step k of the
+ * ramp (k = 0 .. n_steps - 1) uses T0 = t_start + (t_end - t_start)(k + 1/2) /
+ * n_steps for both thermostat half-steps, and Q = N_f k_B T0 tau^2 follows
+ * T0.  xi and eta carry over.  EINVAL for non-finite arguments, tau <= 0,
+ * temperatures <= 0, n_steps < 1 or fewer than two atoms. */
+sevennet_status sevennet_md_set_nose_hoover_ramp(sevennet_md* md, double t_start_K, double t_end_K,
+                                                 int64_t n_steps, double tau_fs);
 /* Thermostat state: xi (1/fs) and eta (dimensionless); the conserved extended
  * energy is E_pot + E_kin + Q xi^2 / 2 + N_f k_B T0 eta.  Synchronises. */
 sevennet_status sevennet_md_get_nose_hoover(const sevennet_md* md, double* xi, double* eta);

@@ -91,6 +91,8 @@ SIGNATURES = {
     "sevennet_eval_decomposed": (_I32, [_P, _I64, _IP, _D, _D, ctypes.c_int32, ctypes.c_int, _D, _D, _D]),
     "sevennet_md_set_skin": (_I32, [_P, ctypes.c_double]),
     "sevennet_md_set_nose_hoover": (_I32, [_P, ctypes.c_double, ctypes.c_double]),
+    "sevennet_md_set_nose_hoover_ramp": (_I32, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                                ctypes.c_double]),
     "sevennet_md_get_nose_hoover": (_I32, [_P, _D, _D]),
     "sevennet_md_get_stats": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "sevennet_md_destroy": (None, [_P]),

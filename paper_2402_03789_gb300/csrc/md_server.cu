@@ -135,6 +135,10 @@ struct sevennet_md {
     bool have_list = false;
     // Nose-Hoover thermostat (tau > 0): {xi, eta} on the device
     double nh_T0 = 0.0, nh_tau = 0.0;
+    // linear ramp of the target from nh_T0 to nh_T1 over nh_ramp steps (0: none);
+    // nh_done steps of it have run
+    double nh_T1 = 0.0;
+    int64_t nh_ramp = 0, nh_done = 0;
     double* nh = nullptr;
     int64_t n_builds = 0, n_edges = 0;
 };
@@ -300,9 +304,16 @@ sevennet_status sevennet_md_step(sevennet_md* md, int64_t n_steps, double dt_fs,
     const int64_t n3 = md->N * 3;
     const unsigned blocks = (unsigned)((n3 + 255) / 256);
     const bool nvt = md->nh_tau > 0.0;
-    const double nf_kt0 = (3.0 * md->N - 3.0) * KB_EV * md->nh_T0;
-    const double q = nf_kt0 * md->nh_tau * md->nh_tau;
     for (int64_t k = 0; k < n_steps; ++k) {
+        // target of this step: the ramp's value at the middle of the step, then its end value
+        double t0 = md->nh_T0;
+        if (md->nh_ramp > 0) {
+            const double x = std::min((double)md->nh_done + 0.5, (double)md->nh_ramp) / (double)md->nh_ramp;
+            t0 = md->nh_T0 + (md->nh_T1 - md->nh_T0) * x;
+            if (md->nh_done < md->nh_ramp) ++md->nh_done;
+        }
+        const double nf_kt0 = (3.0 * md->N - 3.0) * KB_EV * t0;
+        const double q = nf_kt0 * md->nh_tau * md->nh_tau;
         if (nvt) nh_half_kernel<<<1, 1024, 0, md->st>>>(md->N, 0.5 * dt_fs, md->inv_m, md->vel, md->nh, nf_kt0, q);
         kick_drift_kernel<<<blocks, 256, 0, md->st>>>(md->N, dt_fs, md->inv_m, md->f, md->vel, md->pos);
         SN_TRY(md_evaluate(md));
@@ -342,7 +353,24 @@ sevennet_status sevennet_md_set_nose_hoover(sevennet_md* md, double temperature_
     SN_CHECK(tau_fs <= 0.0 || temperature_K > 0.0, SEVENNET_EINVAL, "target temperature must be > 0");
     SN_CHECK(md->N >= 2, SEVENNET_EINVAL, "a thermostat needs at least two atoms");
     md->nh_T0 = temperature_K;
+    md->nh_T1 = temperature_K;
+    md->nh_ramp = md->nh_done = 0;
     md->nh_tau = tau_fs > 0.0 ? tau_fs : 0.0;
+    return SEVENNET_OK;
+}
+
+sevennet_status sevennet_md_set_nose_hoover_ramp(sevennet_md* md, double t_start_K, double t_end_K,
+                                                 int64_t n_steps, double tau_fs) {
+    SN_CHECK(md && std::isfinite(t_start_K) && std::isfinite(t_end_K) && std::isfinite(tau_fs), SEVENNET_EINVAL,
+             "bad argument");
+    SN_CHECK(tau_fs > 0.0 && t_start_K > 0.0 && t_end_K > 0.0 && n_steps >= 1, SEVENNET_EINVAL,
+             "a ramp needs tau > 0, temperatures > 0 and at least one step");
+    SN_CHECK(md->N >= 2, SEVENNET_EINVAL, "a thermostat needs at least two atoms");
+    md->nh_T0 = t_start_K;
+    md->nh_T1 = t_end_K;
+    md->nh_ramp = n_steps;
+    md->nh_done = 0;
+    md->nh_tau = tau_fs;
     return SEVENNET_OK;
 }
 

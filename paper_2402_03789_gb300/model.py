@@ -262,6 +262,36 @@ class MD:
         """Nose-Hoover NVT at temperature_K with time constant tau_fs (tau <= 0: NVE)."""
         L.check(self.lib.sevennet_md_set_nose_hoover(self.handle, float(temperature_K), float(tau_fs)))
 
+    def set_nose_hoover_ramp(self, t_start_K: float, t_end_K: float, n_steps: int, tau_fs: float):
+        """Nose-Hoover NVT whose target ramps linearly from t_start_K to t_end_K
+        over the next n_steps steps (then stays at t_end_K)."""
+        L.check(self.lib.sevennet_md_set_nose_hoover_ramp(self.handle, float(t_start_K), float(t_end_K),
+                                                          int(n_steps), float(tau_fs)))
+
+    def run_schedule(self, segments, dt_fs=1.0, tau_fs=100.0):
+        """Run a temperature schedule under Nose-Hoover NVT, e.g. the melt-quench
+        protocol of Sec. 5.2 (hold at 5000 K, hold at 3000 K, quench at -33 K/ps).
+
+        segments: ("hold", T_K, n_steps) or ("ramp", T_start_K, T_end_K, n_steps).
+        Returns the (E_pot, E_kin) logs of all steps."""
+        eps, eks = [], []
+        for seg in segments:
+            if seg[0] == "hold":
+                _, t, n = seg
+                self.set_nose_hoover(t, tau_fs)
+            elif seg[0] == "ramp":
+                _, t0, t1, n = seg
+                self.set_nose_hoover_ramp(t0, t1, n, tau_fs)
+            else:
+                raise ValueError(f"unknown schedule segment {seg[0]!r}")
+            if n > 0:
+                ep, ek = self.step(int(n), dt_fs)
+                eps.append(ep)
+                eks.append(ek)
+        if not eps:
+            return np.zeros(0), np.zeros(0)
+        return np.concatenate(eps), np.concatenate(eks)
+
     def nose_hoover(self):
         """(xi, eta) of the thermostat."""
         xi = ctypes.c_double()

@@ -48,6 +48,40 @@ def test_nose_hoover_tracks_oracle():
     model.close()
 
 
+def test_nose_hoover_ramp_tracks_oracle():
+    # a melt-quench-style schedule: a 6-step ramp split over two md_step calls,
+    # then a hold at its end value; trajectory and thermostat against the oracle
+    sn, s, spec, w, model = _tiny(200.0)
+    m = s.masses()
+    v = maxwell_boltzmann(m, 1500.0, seed=7)
+    md = sn.MD(model, s.pos, v, s.species, MASSES, s.cell, "fp32")
+    md.set_nose_hoover_ramp(3000.0, 600.0, 6, 10.0)
+    ep1, ek1 = md.step(4, 1.0)
+    ep2, ek2 = md.step(6, 1.0)                     # 2 ramp steps, then 4 at 600 K
+    ep, ek = np.concatenate([ep1, ep2]), np.concatenate([ek1, ek2])
+    p, vv, _ = md.state()
+    xi, eta = md.nose_hoover()
+    po, vo, _, xio, etao, epo, eko, _ = oracle.nose_hoover_nvt(spec, w, s.species, s.pos, v, m, s.cell, 1.0, 10,
+                                                               3000.0, 10.0, t_end_k=600.0, ramp_steps=6)
+    assert abs(xio) > 1e-3
+    assert np.abs(p - po).max() < 1e-6
+    assert np.abs(vv - vo).max() < 1e-7
+    assert abs(xi - xio) < 1e-6 * abs(xio) + 1e-9
+    assert abs(eta - etao) < 1e-6 * abs(etao) + 1e-9
+    assert np.abs(ek - eko).max() / s.n_atoms < 1e-6 * spec.scale
+    assert np.abs(ep - epo).max() / s.n_atoms < 1e-6 * spec.scale
+    # the schedule helper runs the same sequence
+    md2 = sn.MD(model, s.pos, v, s.species, MASSES, s.cell, "fp32")
+    ep3, ek3 = md2.run_schedule([("ramp", 3000.0, 600.0, 6), ("hold", 600.0, 4)], 1.0, 10.0)
+    assert ep3.shape == (10,)
+    assert np.abs(md2.state()[0] - po).max() < 1e-6
+    with pytest.raises(sn.SevenNetError):
+        md2.set_nose_hoover_ramp(3000.0, 600.0, 0, 10.0)
+    md.close()
+    md2.close()
+    model.close()
+
+
 def test_nose_hoover_heats_and_conserves_extended_energy():
     sn, s, spec, w, model = _tiny(1.0)
     m = s.masses()
