@@ -275,76 +275,85 @@ static GateDims gate_dims(const LayerDev& L, int mul0, const int* mul, int lmax)
     return g;
 }
 
+// The gate kernels walk atoms (grid-stride) with the CTA's threads over one
+// atom's row, so no element index is divided by a row length.
+static inline unsigned gate_grid(int64_t n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int64_t g = (int64_t)8 * num_sms(dev);
+    return (unsigned)(n < g ? n : g);
+}
+
 __global__ void gate_fwd_kernel(const GateDims G, int64_t n, const float* __restrict__ y,
                                 float* __restrict__ h) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n * G.h_dim) return;
-    const int64_t v = i / G.h_dim;
-    const int j = (int)(i % G.h_dim);
-    const float* yr = y + v * G.y_dim;
-    if (G.last || j < G.mul0) {
-        h[i] = silu_(yr[j]);
-        return;
+    for (int64_t v = blockIdx.x; v < n; v += gridDim.x) {
+        const float* yr = y + v * G.y_dim;
+        float* hr = h + v * G.h_dim;
+        for (int j = threadIdx.x; j < G.h_dim; j += blockDim.x) {
+            if (G.last || j < G.mul0) {
+                hr[j] = silu_(yr[j]);
+                continue;
+            }
+            const int l = 1 + (G.lmax >= 2 && j >= G.h_off[2]) + (G.lmax >= 3 && j >= G.h_off[3]);
+            const int r = j - irrep_sel(G.h_off, l);
+            const int u = r % irrep_sel(G.mul, l);
+            const float gate = silu_(yr[G.mul0 + irrep_sel(G.goff, l) + u]);
+            hr[j] = yr[irrep_sel(G.y_off, l) + r] * gate;
+        }
     }
-    const int l = 1 + (G.lmax >= 2 && j >= G.h_off[2]) + (G.lmax >= 3 && j >= G.h_off[3]);
-    const int r = j - irrep_sel(G.h_off, l);
-    const int u = r % irrep_sel(G.mul, l);
-    const float gate = silu_(yr[G.mul0 + irrep_sel(G.goff, l) + u]);
-    h[i] = yr[irrep_sel(G.y_off, l) + r] * gate;
 }
 
 void launch_gate_fwd(const LayerDev& L, int mul0, const int* mul, int lmax, int64_t n,
                      const float* y, float* h, cudaStream_t st) {
     const GateDims G = gate_dims(L, mul0, mul, lmax);
-    const int64_t tot = n * G.h_dim;
-    if (tot == 0) return;
-    gate_fwd_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(G, n, y, h);
+    if (n == 0 || G.h_dim == 0) return;
+    gate_fwd_kernel<<<gate_grid(n), 256, 0, st>>>(G, n, y, h);
 }
 
 // gy = dE/dy from gh = dE/dh (or, for the last block, the readout vector)
 __global__ void gate_bwd_kernel(const GateDims G, int64_t n, const float* __restrict__ y,
                                 const float* __restrict__ gh, const float* __restrict__ readout,
                                 float* __restrict__ gy) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n * G.y_dim) return;
-    const int64_t v = i / G.y_dim;
-    const int j = (int)(i % G.y_dim);
-    const float* yr = y + v * G.y_dim;
-    if (G.last) {
-        gy[i] = readout[j] * dsilu_(yr[j]);
-        return;
-    }
-    const float* ghr = gh + v * G.h_dim;
-    if (j < G.mul0) {
-        gy[i] = ghr[j] * dsilu_(yr[j]);
-        return;
-    }
-    if (j < G.mul0 + G.ng) {               // a gate scalar
-        const int gidx = j - G.mul0;
-        const int l = 1 + (G.lmax >= 2 && gidx >= G.goff[2]) + (G.lmax >= 3 && gidx >= G.goff[3]);
-        const int u = gidx - irrep_sel(G.goff, l);
-        const int ml = irrep_sel(G.mul, l), ho = irrep_sel(G.h_off, l), yo = irrep_sel(G.y_off, l);
-        float s = 0.0f;
-        for (int mm = 0; mm < 2 * l + 1; ++mm) {
-            const int off = mm * ml + u;
-            s = fmaf(ghr[ho + off], yr[yo + off], s);
+    for (int64_t v = blockIdx.x; v < n; v += gridDim.x) {
+        const float* yr = y + v * G.y_dim;
+        const float* ghr = gh + v * G.h_dim;
+        float* gyr = gy + v * G.y_dim;
+        for (int j = threadIdx.x; j < G.y_dim; j += blockDim.x) {
+            if (G.last) {
+                gyr[j] = readout[j] * dsilu_(yr[j]);
+                continue;
+            }
+            if (j < G.mul0) {
+                gyr[j] = ghr[j] * dsilu_(yr[j]);
+                continue;
+            }
+            if (j < G.mul0 + G.ng) {               // a gate scalar
+                const int gidx = j - G.mul0;
+                const int l = 1 + (G.lmax >= 2 && gidx >= G.goff[2]) + (G.lmax >= 3 && gidx >= G.goff[3]);
+                const int u = gidx - irrep_sel(G.goff, l);
+                const int ml = irrep_sel(G.mul, l), ho = irrep_sel(G.h_off, l), yo = irrep_sel(G.y_off, l);
+                float s = 0.0f;
+                for (int mm = 0; mm < 2 * l + 1; ++mm) {
+                    const int off = mm * ml + u;
+                    s = fmaf(ghr[ho + off], yr[yo + off], s);
+                }
+                gyr[j] = s * dsilu_(yr[j]);
+                continue;
+            }
+            const int l = 1 + (G.lmax >= 2 && j >= G.y_off[2]) + (G.lmax >= 3 && j >= G.y_off[3]);
+            const int r = j - irrep_sel(G.y_off, l);
+            const int u = r % irrep_sel(G.mul, l);
+            gyr[j] = ghr[irrep_sel(G.h_off, l) + r] * silu_(yr[G.mul0 + irrep_sel(G.goff, l) + u]);
         }
-        gy[i] = s * dsilu_(yr[j]);
-        return;
     }
-    const int l = 1 + (G.lmax >= 2 && j >= G.y_off[2]) + (G.lmax >= 3 && j >= G.y_off[3]);
-    const int r = j - irrep_sel(G.y_off, l);
-    const int u = r % irrep_sel(G.mul, l);
-    gy[i] = ghr[irrep_sel(G.h_off, l) + r] * silu_(yr[G.mul0 + irrep_sel(G.goff, l) + u]);
 }
 
 void launch_gate_bwd(const LayerDev& L, int mul0, const int* mul, int lmax, int64_t n,
                      const float* y, const float* gh, const float* readout, float* gy,
                      cudaStream_t st) {
     const GateDims G = gate_dims(L, mul0, mul, lmax);
-    const int64_t tot = n * G.y_dim;
-    if (tot == 0) return;
-    gate_bwd_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(G, n, y, gh, readout, gy);
+    if (n == 0 || G.y_dim == 0) return;
+    gate_bwd_kernel<<<gate_grid(n), 256, 0, st>>>(G, n, y, gh, readout, gy);
 }
 
 // ---------------------------------------------------------------- readout
@@ -405,41 +414,54 @@ void launch_forces(int64_t n, const int* row_ptr, const int* rev, const float* g
     forces_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, row_ptr, rev, gd, geom, f_s, w_atom);
 }
 
-// One CTA per structure: fixed-order FP64 sums of atom energies and virials.
-__global__ void reduce_structs_kernel(const int64_t* __restrict__ atom_off,
-                                      const double* __restrict__ e_atom,
-                                      const double* __restrict__ w_atom, double* __restrict__ energy,
-                                      double* __restrict__ virial) {
+// One CTA per structure: fixed-order FP64 sums of atom energies and virials
+// (per thread over a strided set of atoms, then a fixed shuffle tree per warp
+// and over the warps), so repeated evaluations give identical sums.
+constexpr int RS_THREADS = 1024;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) reduce_structs_kernel(const int64_t* __restrict__ atom_off,
+                                                                    const double* __restrict__ e_atom,
+                                                                    const double* __restrict__ w_atom,
+                                                                    double* __restrict__ energy,
+                                                                    double* __restrict__ virial) {
     const int s = blockIdx.x;
     const int64_t a0 = atom_off[s], a1 = atom_off[s + 1];
     double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int64_t v = a0 + threadIdx.x; v < a1; v += blockDim.x) {
+#pragma unroll 4
+    for (int64_t v = a0 + threadIdx.x; v < a1; v += RS_THREADS) {
         acc[0] += e_atom[v];
 #pragma unroll
         for (int k = 0; k < 9; ++k) acc[1 + k] += w_atom[v * 9 + k];
     }
-    __shared__ double red[10][256];
+    __shared__ double red[RS_THREADS / 32][10];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 10; ++k) red[k][threadIdx.x] = acc[k];
-    __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if ((int)threadIdx.x < st) {
-#pragma unroll
-            for (int k = 0; k < 10; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + st];
-        }
-        __syncthreads();
+    for (int k = 0; k < 10; ++k) {
+        const double w = warp_sum_d(acc[k]);
+        if (lane == 0) red[warp][k] = w;
     }
-    if (threadIdx.x == 0) {
-        if (energy) energy[s] = red[0][0];
-        if (virial)
-            for (int k = 0; k < 9; ++k) virial[s * 9 + k] = red[1 + k][0];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) acc[k] = warp_sum_d(red[lane][k]);
+        if (lane == 0) {
+            if (energy) energy[s] = acc[0];
+            if (virial)
+                for (int k = 0; k < 9; ++k) virial[s * 9 + k] = acc[1 + k];
+        }
     }
 }
 
 void launch_reduce_structs(int32_t n_structs, const int64_t* atom_off, const double* e_atom,
                            const double* w_atom, double* energy, double* virial, cudaStream_t st) {
     if (n_structs == 0) return;
-    reduce_structs_kernel<<<n_structs, 256, 0, st>>>(atom_off, e_atom, w_atom, energy, virial);
+    reduce_structs_kernel<<<n_structs, RS_THREADS, 0, st>>>(atom_off, e_atom, w_atom, energy, virial);
 }
 
 __global__ void scatter_forces_kernel(int64_t n, const int* __restrict__ perm,
