@@ -670,6 +670,7 @@ sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const do
         }
         D.W = col;
         D.Wpad = ((col + 3) & ~3) + 4;
+        D.WpadB = ((col + 7) & ~7) + 8;
         D.H = H;
         D.n_basis = NB;
         D.lmax = cfg->lmax;

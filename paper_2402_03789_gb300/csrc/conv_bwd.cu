@@ -137,7 +137,7 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
                 float* __restrict__ gx, float* __restrict__ gd) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    const ConvSmem L = conv_smem_layout(D.Wpad, H, D.nG, D.ys, true, BF);
+    const ConvSmem L = conv_smem_layout(D.Wpad, D.WpadB, H, D.nG, D.ys, true, BF);
     __shared__ int s_range[2];
     cta_range(n_atoms, n_edges, row_ptr, s_range);
     const int v0 = s_range[0], v1 = s_range[1];
@@ -159,7 +159,7 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
         // dE/dd of the blocks done so far, copied to shared memory for phase G
         if (t < 3 * ne) cp_async4(s_gdp + t, gd + (size_t)c0 * 3 + t);
         cp_async_commit();
-        if constexpr (BF) chunk_w_gemm_bf16<H>(D, L, smem, W3T_h);
+        if constexpr (BF) chunk_w_gemm_bf16<H, false>(D, L, smem, W3T_h);
         else chunk_w_gemm_f32<H>(D, L, smem, W3);
         // E: per-edge adjoint of the tensor product (path lists fixed per block kind);
         // the H = 32 kernels (small models) take one channel per lane

@@ -66,12 +66,12 @@ __device__ __forceinline__ void hk_inv(int i, int& k, int& e) {
 // the FP32 phases D and F on the FP32 path only.  dE/dH2 (adjoint) reuses H2,
 // which is dead once phase D has run.  The BF16 kernels stay under 97 KB so two
 // CTAs leave about 60 KB of each SM's 256 KB to the L1 cache.
-__host__ __device__ inline ConvSmem conv_smem_layout(int Wpad, int H, int nG, int ys, bool bwd, bool bf) {
+__host__ __device__ inline ConvSmem conv_smem_layout(int Wpad, int WpadB, int H, int nG, int ys, bool bwd, bool bf) {
     ConvSmem s;
     int o = 0;
     const int stage_bf = H * EC > MAX_NB * EC ? H * EC : MAX_NB * EC;
     const int stage_f32 = KS * DCOLS > 2 * CS * 64 ? KS * DCOLS : 2 * CS * 64;
-    s.w = o;     o += EC * Wpad;
+    s.w = o;     o += (bf && !bwd) ? EC * WpadB / 2 : EC * Wpad;   // [EC][row stride]: BF16 in the BF16 forward
     s.stage = o; o += bf ? stage_bf : (stage_f32 > stage_bf ? stage_f32 : stage_bf);
     s.A1 = o;    o += H * EC;
     s.A2 = o;    o += H * EC;
@@ -210,6 +210,21 @@ struct BlockPaths {
 };
 
 // ---- BF16 tensor-core variants of phases D and F (mma.sync m16n8k16, FP32 accumulate)
+// The per-edge weight tile holds BF16 values in the BF16 forward kernel and
+// FP32 values otherwise (the adjoint keeps dE/dw in FP32 beside w).
+template <bool BF>
+struct WTile {
+    using T = float;
+};
+template <>
+struct WTile<true> {
+    using T = __nv_bfloat16;
+};
+__device__ __forceinline__ float wload(const float* p) { return *p; }
+__device__ __forceinline__ float wload(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void wstore(float* p, float v) { *p = v; }
+__device__ __forceinline__ void wstore(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&v);
@@ -236,7 +251,7 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint
 
 // Phase D (BF16): w[e][c] = sum_k H2[k][e] W3[k][c]; B operand W3T [W][H] (bf16).
 // Each warp loads the B fragments of four n tiles at once.
-template <int H>
+template <int H, bool BFT>
 __device__ __forceinline__ void chunk_w_gemm_bf16(const ConvDesc& D, const ConvSmem& L, float* smem,
                                                   const __nv_bfloat16* __restrict__ W3T) {
     constexpr int KSN = H / 16;                // k steps (4 or 2)
@@ -245,7 +260,6 @@ __device__ __forceinline__ void chunk_w_gemm_bf16(const ConvDesc& D, const ConvS
     static_assert(EC == 16, "one m tile of edges");
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tq = lane & 3;
     const float* s_H2 = smem + L.H2;
-    float* s_w = smem + L.w;
     uint32_t af[KSN][4];
 #pragma unroll
     for (int ks = 0; ks < KSN; ++ks) {
@@ -279,8 +293,16 @@ __device__ __forceinline__ void chunk_w_gemm_bf16(const ConvDesc& D, const ConvS
                 mma_bf16(c, af[ks], b);
             }
             const int col = nt * 8 + 2 * tq;
-            *reinterpret_cast<float2*>(s_w + g * D.Wpad + col) = make_float2(c[0], c[1]);
-            *reinterpret_cast<float2*>(s_w + (g + 8) * D.Wpad + col) = make_float2(c[2], c[3]);
+            if constexpr (BFT) {         // BF16 tile [EC][WpadB]
+                __nv_bfloat16* s_w = reinterpret_cast<__nv_bfloat16*>(smem + L.w);
+                *reinterpret_cast<__nv_bfloat162*>(s_w + g * D.WpadB + col) = __floats2bfloat162_rn(c[0], c[1]);
+                *reinterpret_cast<__nv_bfloat162*>(s_w + (g + 8) * D.WpadB + col) =
+                    __floats2bfloat162_rn(c[2], c[3]);
+            } else {                     // FP32 tile [EC][Wpad]
+                float* s_w = smem + L.w;
+                *reinterpret_cast<float2*>(s_w + g * D.Wpad + col) = make_float2(c[0], c[1]);
+                *reinterpret_cast<float2*>(s_w + (g + 8) * D.Wpad + col) = make_float2(c[2], c[3]);
+            }
         }
     }
     __syncthreads();
@@ -296,7 +318,7 @@ __device__ __forceinline__ void chunk_gw_gemm_bf16(const ConvDesc& D, const Conv
     constexpr int NT = H / 8;                  // n tiles of 8 hidden units
     static_assert(EC == 16, "one m tile of edges");
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tq = lane & 3;
-    const float* s_w = smem + L.w;
+    const float* s_w = smem + L.w;             // dE/dw, [EC][Wpad]
     float* s_gH = smem + L.gH;                 // [H][EC]
     const int W = D.W;
     for (int i = t; i < H * EC; i += CONV_THREADS) s_gH[i] = 0.0f;
@@ -673,7 +695,7 @@ __device__ __forceinline__ void chunk_gw_gemm_f32(const ConvDesc& D, const ConvS
 
 
 static inline size_t smem_bytes(const ConvDesc& D, int H, bool bwd, bool bf) {
-    return (size_t)conv_smem_layout(D.Wpad, H, D.nG, D.ys, bwd, bf).total * sizeof(float);
+    return (size_t)conv_smem_layout(D.Wpad, D.WpadB, H, D.nG, D.ys, bwd, bf).total * sizeof(float);
 }
 
 static inline int conv_grid(int64_t n_atoms, int ctas_per_sm) {

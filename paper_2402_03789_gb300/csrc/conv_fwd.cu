@@ -30,8 +30,8 @@ __host__ __device__ constexpr int fwd_acc_off(int j, int i) {
 // changes.  A receiver that started in this CTA's previous chunk was written
 // there by this same thread; its partial sums seed the registers, loaded
 // before the first gathers so the two overlap.
-template <int L1, int LMAX, int KIND, int J, int CPL>
-__device__ __forceinline__ void tp_fwd_set(const ConvDesc& D, int u0, int ne, const float* s_w,
+template <int L1, int LMAX, int KIND, int J, int CPL, typename WT>
+__device__ __forceinline__ void tp_fwd_set(const ConvDesc& D, int u0, int ne, const WT* s_w,
                                            const float* s_G, const int* s_src, const int* s_dst,
                                            const int* s_first, const float* __restrict__ x,
                                            float* __restrict__ m) {
@@ -43,7 +43,7 @@ __device__ __forceinline__ void tp_fwd_set(const ConvDesc& D, int u0, int ne, co
     constexpr int NACC = fwd_set_nacc(L1, LMAX, KIND, J);
     constexpr int PF = (CPL * N1 <= 2) ? 4 : 2;           // edges whose gathers are in flight together
     const int mul = D.mul_in[L1];
-    const int Wpad = D.Wpad, nG = D.nG, m_dim = D.m_dim, x_dim = D.x_dim;
+    const int Wpad = sizeof(WT) == 2 ? D.WpadB : D.Wpad, nG = D.nG, m_dim = D.m_dim, x_dim = D.x_dim;
     const float* xb = x + D.x_off[L1] + u0;
     float acc[CPL][NACC];
     auto rows = [&](int v, auto&& f) {        // f(path P, acc offset, N3) for every path of the set
@@ -96,10 +96,10 @@ __device__ __forceinline__ void tp_fwd_set(const ConvDesc& D, int u0, int ne, co
             const PathDesc& P = D.paths[BP::begin + i];
             float G[((N1 * N3 + 3) / 4) * 4];
             load_G<N1 * N3>(s_G + e * nG + P.g_off, G);
-            const float* wr = s_w + e * Wpad + P.col0 + u0;
+            const WT* wr = s_w + e * Wpad + P.col0 + u0;
 #pragma unroll
             for (int k = 0; k < CPL; ++k) {
-                const float wv = wr[32 * k];
+                const float wv = wload(wr + 32 * k);
 #pragma unroll
                 for (int c = 0; c < N3; ++c) {
                     float tt = 0.0f;
@@ -147,8 +147,8 @@ __device__ __forceinline__ void tp_fwd_set(const ConvDesc& D, int u0, int ne, co
 }
 
 // Phase E of the forward: every warp runs its work sets over the chunk.
-template <int H, int LMAX, int KIND>
-__device__ __forceinline__ void tp_fwd_chunk(const ConvDesc& D, int ne, const float* s_w, const float* s_G,
+template <int H, int LMAX, int KIND, typename WT>
+__device__ __forceinline__ void tp_fwd_chunk(const ConvDesc& D, int ne, const WT* s_w, const float* s_G,
                                              const int* s_src, const int* s_dst, const int* s_first,
                                              const float* __restrict__ x, float* __restrict__ m) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -166,7 +166,7 @@ __device__ __forceinline__ void tp_fwd_chunk(const ConvDesc& D, int ne, const fl
                         constexpr int LC = decltype(Cc)::value;
                         if constexpr (fwd_cpl_compiled(H, L1, NACC, 1 << LC)) {
                             if (l1 == L1 && set == J && lc == LC)
-                                tp_fwd_set<L1, LMAX, KIND, J, (1 << LC)>(D, u0, ne, s_w, s_G, s_src, s_dst,
+                                tp_fwd_set<L1, LMAX, KIND, J, (1 << LC), WT>(D, u0, ne, s_w, s_G, s_src, s_dst,
                                                                         s_first, x, m);
                         }
                     });
@@ -186,7 +186,9 @@ conv_fwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
                 const float* __restrict__ x, float* __restrict__ m) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    const ConvSmem L = conv_smem_layout(D.Wpad, H, D.nG, D.ys, false, BF);
+    const ConvSmem L = conv_smem_layout(D.Wpad, D.WpadB, H, D.nG, D.ys, false, BF);
+    using WT = typename WTile<BF>::T;
+    const WT* s_w = reinterpret_cast<const WT*>(smem + L.w);
     __shared__ int s_range[2];
     cta_range(n_atoms, n_edges, row_ptr, s_range);
     const int v0 = s_range[0], v1 = s_range[1];
@@ -209,13 +211,13 @@ conv_fwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
         __syncthreads();
         chunk_prologue<H, BF, LMAX>(D, L, smem, c0, ne, pf, W2, W2T_h);
         pf.fetch(c0 + EC, E1, dst, src, geom, row_ptr);   // next chunk's edges, in flight meanwhile
-        if constexpr (BF) chunk_w_gemm_bf16<H>(D, L, smem, W3T_h);
+        if constexpr (BF) chunk_w_gemm_bf16<H, true>(D, L, smem, W3T_h);
         else chunk_w_gemm_f32<H>(D, L, smem, W3);
         switch (D.kind) {
-            case 0: tp_fwd_chunk<H, LMAX, 0>(D, ne, smem + L.w, smem + L.G, s_src, s_dst, s_first, x, m); break;
-            case 1: tp_fwd_chunk<H, LMAX, 1>(D, ne, smem + L.w, smem + L.G, s_src, s_dst, s_first, x, m); break;
-            case 2: tp_fwd_chunk<H, LMAX, 2>(D, ne, smem + L.w, smem + L.G, s_src, s_dst, s_first, x, m); break;
-            default: tp_fwd_chunk<H, LMAX, 3>(D, ne, smem + L.w, smem + L.G, s_src, s_dst, s_first, x, m); break;
+            case 0: tp_fwd_chunk<H, LMAX, 0, WT>(D, ne, s_w, smem + L.G, s_src, s_dst, s_first, x, m); break;
+            case 1: tp_fwd_chunk<H, LMAX, 1, WT>(D, ne, s_w, smem + L.G, s_src, s_dst, s_first, x, m); break;
+            case 2: tp_fwd_chunk<H, LMAX, 2, WT>(D, ne, s_w, smem + L.G, s_src, s_dst, s_first, x, m); break;
+            default: tp_fwd_chunk<H, LMAX, 3, WT>(D, ne, s_w, smem + L.G, s_src, s_dst, s_first, x, m); break;
         }
     }
 }

@@ -181,7 +181,7 @@ struct PathDesc {
 struct ConvDesc {
     int32_t n_paths;
     int32_t W;          // radial MLP output width (sum of path channels)
-    int32_t Wpad;       // row stride of the per-edge weight tile in shared memory
+    int32_t Wpad;       // row stride (floats) of the per-edge weight tile in shared memory (FP32 tile)
     int32_t H;          // hidden width of the radial MLP
     int32_t n_basis;
     int32_t lmax;       // spherical-harmonic degree
@@ -200,6 +200,7 @@ struct ConvDesc {
     PathDesc paths[MAX_PATHS];
     int16_t n_slots[CONV_WARPS];
     int16_t slot_group[CONV_WARPS][MAX_SLOTS];  // (l1 << 11) | (set << 8) | (channel block << 2) | log2 CPL
+    int32_t WpadB;      // row stride (BF16 values) of the BF16 weight tile: rows start on 16 bytes
 };
 
 // One row-block matrix product of a per-irrep linear: rows are (atom, m)
