@@ -164,7 +164,7 @@ __global__ void gather_kernel(int64_t n, int S, const int64_t* __restrict__ atom
 // candidates clearly outside r_c; its margin, 1e-3 A + 1e-6 (|q_v| + |S~ cell| +
 // r_c), is over ten times the FP32 rounding of d for any coordinates (positions
 // along non-periodic directions are not wrapped), so it cannot drop an edge.
-constexpr int NGL = 8;
+constexpr int NGL = 2;
 
 __device__ __forceinline__ int floor_div(int a, int n) { return a >= 0 ? a / n : -((n - 1 - a) / n); }
 
