@@ -1,7 +1,8 @@
 """Full-size workloads (24,000-atom SiO2, 112,000-atom Si3N4) in the launch
 configuration bench.py times: the edge set against the oracle's neighbour
 list, and properties that hold at any size (zero net force, symmetric
-virial, translation invariance, BF16 within the force tolerance of FP32)."""
+virial, translation invariance, rotation equivariance, permutation invariance,
+BF16 within the force tolerance of FP32)."""
 
 import numpy as np
 import pytest
@@ -55,3 +56,25 @@ def test_full_size_properties(name):
     Et, Ft, Wt = model.evaluate(s.pos + np.array([0.37, -1.21, 2.9]), s.cell, s.species, "fp32")
     assert abs(Et - E32) / s.n_atoms <= 1e-6
     assert np.linalg.norm(Ft - F32) / np.linalg.norm(F32) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["sio2_24000", "si3n4_112000"])
+def test_full_size_rotation_and_permutation(name):
+    # E is invariant and F, W equivariant under a rotation of positions and cell
+    # (r -> R r); a permutation of the input atoms permutes the forces.  Both
+    # hold at any size, in the FP32 path's tolerances.
+    from scipy.spatial.transform import Rotation
+    s, spec = _work(name)
+    model = get_model(spec)
+    n = s.n_atoms
+    E, F, W = model.evaluate(s.pos, s.cell, s.species, "fp32")
+    R = Rotation.random(random_state=17).as_matrix()
+    Er, Fr, Wr = model.evaluate(s.pos @ R.T, s.cell @ R.T, s.species, "fp32")
+    assert abs(Er - E) / n <= 1e-6
+    assert np.linalg.norm(Fr - F @ R.T) / np.linalg.norm(F) <= 1e-5
+    assert np.linalg.norm(Wr - R @ W @ R.T) / np.linalg.norm(W) <= 1e-5
+    p = np.random.default_rng(18).permutation(n)
+    Ep, Fp, Wp = model.evaluate(s.pos[p], s.cell, np.asarray(s.species)[p], "fp32")
+    assert abs(Ep - E) / n <= 1e-6
+    assert np.linalg.norm(Fp - F[p]) / np.linalg.norm(F) <= 1e-5
+    assert np.linalg.norm(Wp - W) / np.linalg.norm(W) <= 1e-5
