@@ -110,8 +110,9 @@ __device__ __forceinline__ void mma_bf16_n(float* c, const uint32_t* a, const ui
 }
 
 // 128 x 64 output tile, 8 warps as 4 (rows) x 2 (cols), each warp 32 rows x 32
-// cols (2 m tiles x 4 n tiles).  K runs in blocks of 32 under one k permutation
-// of both operands (the reduction order inside an MMA is free): lane tq owns
+// cols (2 m tiles x 4 n tiles); for N <= 32 the warps stack 8 x 1 over 256 x 32.
+// K runs in blocks of 32 under one k permutation of both operands (the
+// reduction order inside an MMA is free): lane tq owns
 // k = kb + 8 tq + [0, 8), k step ks takes kb + 8 tq + 4 ks + [0, 4).  Its A
 // values are then one float4 per row and k step, and its B words (hi and lo)
 // one 16-byte load per n row and k block.  K and N are multiples of 32.
@@ -119,11 +120,14 @@ __global__ void __launch_bounds__(256)
 gemm_bf16_kernel(const GemmBatch batch) {
     const GemmProb& P = batch.p[blockIdx.z];
     const int64_t rows = P.n_atoms * P.R;
-    const int64_t r0 = (int64_t)blockIdx.x * 128;
+    // N <= 32: the 8 warps stack as 8 x 1 over a 256 x 32 tile (the grid's extra
+    // row blocks exit); otherwise 4 x 2 over 128 x 64
+    const bool narrow = P.N <= 32;
+    const int64_t r0 = (int64_t)blockIdx.x * (narrow ? 256 : 128);
     const int n0 = blockIdx.y * 64;
     if (r0 >= rows || n0 >= P.N) return;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tq = lane & 3;
-    const int wr = warp & 3, wc = warp >> 2;
+    const int wr = narrow ? warp : (warp & 3), wc = narrow ? 0 : (warp >> 2);
     const int nbase = n0 + wc * 32;
     if (nbase >= P.N) return;
     auto rowptr = [&](int64_t r) -> const float* {
