@@ -183,7 +183,7 @@ sevennet_status sevennet_eval_batch_dev(sevennet_model* model, int32_t n_structs
  *   x [n_atoms][x_dim] FP32 block input after linear_1, irreps stored as
  *     [l][m][channel] blocks; m_out [n_atoms][m_dim] FP32 messages, paths
  *     concatenated per l3 in path order.
- * Backward: given g_m, writes g_x (overwritten) and adds dE/dd into g_d
+ * Backward (the adjoint, Eqs. 5 and 8): given g_m, writes g_x (overwritten) and adds dE/dd into g_d
  * (accumulated; zero it first).  prec selects the radial-MLP arithmetic.
  * Both are ordered on `stream` (NULL = the CUDA default stream) and return
  * without synchronising. */
