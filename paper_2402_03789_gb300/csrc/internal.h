@@ -352,7 +352,7 @@ sevennet_status refresh_neighbors(sevennet_model* M, Workspace* ws, int64_t n_at
                                   const int* list_row_ptr, const int* list_src, const int* list_shift,
                                   cudaStream_t st, int64_t* n_edges_out);
 
-// The steps of run_model, for drivers that interleave work between blocks
+// The steps of run_model, for callers that interleave work between blocks
 // (the domain-decomposed evaluation): all operate on the N atoms and E edges of
 // the workspace's graph.
 void model_embed(sevennet_model* M, Workspace* ws, int64_t N, cudaStream_t st);
