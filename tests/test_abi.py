@@ -70,3 +70,19 @@ def test_padding_walker_matches_oracle_layout():
         spec_p, w_p = padding.pad_model(spec, np.arange(oracle.n_params(spec), dtype=np.float64))
         assert all(m % 32 == 0 for m in spec_p.mul)
         assert w_p.size == oracle.n_params(spec_p)
+
+
+def test_padded_model_is_exact_in_the_oracle():
+    # zero-padding a small-channel model to multiples of 32 leaves E, F and W
+    # unchanged: the padded channels stay zero through every operation
+    from synth import benchmark_model, make_quartz, normal_weights
+    from paper_2402_03789_gb300 import padding
+    s = make_quartz("quartz_216")
+    for spec in (benchmark_model(2, 8, lmax=2), benchmark_model(2, 4, lmax=3)):
+        w = normal_weights(oracle.n_params(spec))
+        spec_p, w_p = padding.pad_model(spec, w)
+        E, F, W, *_ = oracle.energy_forces_virial(spec, w, s.species, s.pos, s.cell)
+        Ep, Fp, Wp, *_ = oracle.energy_forces_virial(spec_p, w_p, s.species, s.pos, s.cell)
+        assert abs(Ep - E) <= 1e-9 * max(1.0, abs(E))
+        assert np.abs(Fp - F).max() <= 1e-9 * max(1e-12, np.abs(F).max())
+        assert np.abs(Wp - W).max() <= 1e-9 * max(1e-12, np.abs(W).max())
