@@ -26,11 +26,16 @@ Pins (tests/test_oracle_*.py): parameter count 842,432 = "0.84 million"
 (Sec. 5.1); rotation / translation / permutation invariance; extensivity;
 zero net force; forces and virial against central finite differences;
 closed-form messages of one edge for the identity / dot / cross couplings.
-Parity unpinned: the normalisation constants (1/sqrt(fan_in) of the MLP and
-linears, 1/avg_num_neigh, the readout widths), the SiLU activations of the gate
-and the envelope order p are readings of points the paper leaves open; no
-reference values of the real SevenNet exist to pin them, so they are fixed only
-by agreement between this oracle and the CUDA library.
+The readings of points the paper leaves open are pinned structurally in
+tests/test_oracle_readings.py: gate() (SiLU scalars, SiLU gates in the order
+[scalars | gates of l = 1 | gates of l = 2 ...], one open gate lets exactly its
+channel through), radial_mlp() (one-hot basis through unit weights gives
+SiLU(SiLU(1/sqrt(n_basis))/sqrt(H))/sqrt(H); no biases), the message sum over
+the constant avg_num_neigh = 34.0, and the readout's two plain linears; each
+pin fails under the planted alternatives (no SiLU, sigmoid gates, swapped gate
+blocks, 1/fan_in, an output activation, biases, 1/sqrt(avg_num_neigh), a
+per-structure degree).  What no test can pin is agreement with the trained
+SevenNet's own numbers: no reference weights or printed values exist.
 
 Canonical weight order (one flat FP64 vector): embed [n_species, mul0]; then per
 block: sc[l] [mul_in, mul_y] for l in Y and In (ascending l), lin1[l] [mul, mul]

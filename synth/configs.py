@@ -67,8 +67,8 @@ MODEL_SEVENNET0_89 = ModelSpec(n_species=89, n_layers=5, mul=(128, 64, 32),
 
 # Shapes of the paper's scaling benchmarks (Sec. 4): channel counts 4-64 for
 # every irrep, 2-5 message-passing layers, lmax 3, cutoff 4.0 A, on alpha-quartz
-# SiO2.  Here lmax is at most 2 and channels are multiples of 32 (what the GPU
-# kernels are compiled for).  avg_num_neigh 21.4 is the mean neighbour count
+# SiO2.  lmax may be 1, 2 or 3; channel counts below 32 run on the GPU as the
+# exactly zero-padded 32-channel model.  avg_num_neigh 21.4 is the mean neighbour count
 # within 4 A at 2.65 g/cm3 (4/3 pi r_c^3 x 0.0797 atoms/A^3), a normalisation
 # constant like SevenNet-0's.
 def benchmark_model(n_layers: int, channels: int, lmax: int = 2) -> "ModelSpec":
