@@ -343,6 +343,17 @@ sevennet_status sevennet_profile_read(sevennet_model* model, int32_t n_max, char
                                       double* total_ms, int64_t* launches, int32_t* n_out);
 int64_t sevennet_launch_count(void);
 
+/* FP32 ALU throughput of `device`, measured: a grid of 4 CTAs x 256 threads per
+ * SM, each thread updating 16 independent register-resident FMA chains `iters`
+ * times (packed = 0: fma.rn.f32; packed = 1: fma.rn.f32x2, two FMAs per
+ * instruction).  One untimed warm-up launch, then one launch timed with CUDA
+ * events on a private stream.  Writes the FLOPs of the timed launch (2 per FMA)
+ * and its milliseconds.  It is the denominator of the ALU roofline of the
+ * FP32 path and of the tensor-product phases (the paper gives no kernel-level
+ * figure; this is a property of the device).  Allocates and frees one small
+ * device buffer; EINVAL for null outputs or iters <= 0, ECUDA on a CUDA error. */
+sevennet_status sevennet_fp32_peak(int32_t device, int32_t packed, int32_t iters, double* flop, double* ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -104,6 +104,7 @@ SIGNATURES = {
     "sevennet_profile": (_I32, [_P, _I32]),
     "sevennet_profile_read": (_I32, [_P, _I32, ctypes.c_char_p, _D, ctypes.POINTER(_I64), _IP]),
     "sevennet_launch_count": (_I64, []),
+    "sevennet_fp32_peak": (_I32, [_I32, _I32, _I32, _D, _D]),
 }
 
 _lib = None

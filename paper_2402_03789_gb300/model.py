@@ -171,6 +171,14 @@ class SevenNet:
     def launch_count():
         return int(L.load().sevennet_launch_count())
 
+    @staticmethod
+    def fp32_peak(device=0, packed=False, iters=20000):
+        """Measured FP32 FMA throughput of the device: (TFLOP/s, flop, ms)."""
+        flop, ms = ctypes.c_double(), ctypes.c_double()
+        L.check(L.load().sevennet_fp32_peak(int(device), int(bool(packed)), int(iters),
+                                            ctypes.byref(flop), ctypes.byref(ms)))
+        return flop.value / (ms.value * 1e-3) / 1e12, flop.value, ms.value
+
     # -------------------------------------------------------------- device API
     def evaluate_batch_dev(self, atom_offsets, cells, species, pos, precision="fp32", pbc=None,
                            stream=None, out=None):
