@@ -45,13 +45,15 @@ sevennet_status conv_configure_bwd(int H, size_t need);
 size_t conv_smem_bytes(const ConvDesc& D, int H, bool bwd);
 
 sevennet_status conv_configure(int H, const std::vector<LayerDev>& layers) {
-    size_t need_f = 0, need_b = 0;
+    size_t need_f = 0, need_b = 0, need_tc = 0;
     for (const LayerDev& L : layers) {
         need_f = std::max(need_f, conv_smem_bytes(L.conv, H, false));
         need_b = std::max(need_b, conv_smem_bytes(L.conv, H, true));
+        if (L.conv.tc_ok) need_tc = std::max(need_tc, conv_tc_smem_bytes(L.conv, H));
     }
     SN_TRY(conv_configure_fwd(H, need_f));
     SN_TRY(conv_configure_bwd(H, need_b));
+    if (need_tc) SN_TRY(conv_configure_fwd_tc(H, need_tc));
     return SEVENNET_OK;
 }
 
@@ -294,6 +296,60 @@ static bool assign_slots(ConvDesc& D, int H) {
     if (best < 0) return false;
     build(best_choice, sl);
     return lpt(sl, D.slot_group, D.n_slots) >= 0;
+}
+
+// Tensor-core forward tables: B-fragment offsets per path, the staged x
+// regions (row strides chosen so that the lanes of a warp read distinct
+// shared-memory banks) and the work units (one path set over 16 channels),
+// assigned longest-first to the warps.  Blocks with lmax 3, multiplicities not
+// divisible by 16 or more shared memory than two CTAs per SM allow keep the
+// FFMA forward (tc_ok = 0).
+static void assign_tc(ConvDesc& D, int H) {
+    D.tc_ok = 0;
+    if (D.lmax > 2) return;
+    int words = 0, xo = 0;
+    for (int l = 0; l < NL; ++l) { D.xs_off[l] = 0; D.xs_stride[l] = 0; }
+    for (int l1 = 0; l1 <= D.lmax; ++l1) {
+        if (!D.mul_in[l1]) continue;
+        if (D.mul_in[l1] % 16) return;
+        const int n1 = 2 * l1 + 1;
+        for (int p = D.pbeg[l1]; p < D.pend[l1]; ++p) {
+            D.paths[p].b_off = words;
+            words += tc_nkg(n1) * 64;
+        }
+        const int len = n1 * D.mul_in[l1];
+        int stride = len;
+        if (n1 == 1) { while (stride % 16 != 4) stride += 4; }
+        else { while (stride % 32 != 8) stride += 4; }
+        D.xs_off[l1] = xo;
+        D.xs_stride[l1] = stride;
+        xo += EC * stride;
+    }
+    D.nBF = words;
+    D.xs_total = xo;
+    if (conv_tc_smem_bytes(D, H) > 112 * 1024) return;
+    struct Unit { int code, load; };
+    std::vector<Unit> units;
+    for (int l1 = 0; l1 <= D.lmax; ++l1) {
+        if (!D.mul_in[l1] || D.pend[l1] <= D.pbeg[l1]) continue;
+        const PathSets S = tc_path_sets(l1, D.lmax, D.kind);
+        const int nkg = tc_nkg(2 * l1 + 1);
+        for (int j = 0; j < S.n; ++j)
+            for (int tile = 0; tile < D.mul_in[l1] / 16; ++tile)
+                units.push_back({(l1 << 12) | (j << 8) | tile, (S.b[j + 1] - S.b[j]) * nkg + 2});
+    }
+    std::stable_sort(units.begin(), units.end(), [](const Unit& a, const Unit& b) { return a.load > b.load; });
+    int load[CONV_WARPS] = {0}, cnt[CONV_WARPS] = {0};
+    for (const Unit& u : units) {
+        int best = -1;
+        for (int w = 0; w < CONV_WARPS; ++w)
+            if (cnt[w] < MAX_SLOTS_TC && (best < 0 || load[w] < load[best])) best = w;
+        if (best < 0) return;
+        D.slot_tc[best][cnt[best]++] = (int16_t)u.code;
+        load[best] += u.load;
+    }
+    for (int w = 0; w < CONV_WARPS; ++w) D.n_slots_tc[w] = (int16_t)cnt[w];
+    D.tc_ok = 1;
 }
 
 }  // namespace sn
@@ -685,6 +741,7 @@ sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const do
         D.env_c = (float)(p * (p + 1.0) / 2.0);
         D.poly_p = cfg->poly_p;
         if (!assign_slots(D, H)) { set_error("block %d: too many channel groups", t); return fail(SEVENNET_EINVAL); }
+        assign_tc(D, H);
         // weights
         const std::string pre = "L" + std::to_string(t) + ".";
         sevennet_status s;

@@ -271,9 +271,15 @@ void launch_conv_fwd(const LayerDev& L, int H, sevennet_precision prec, int64_t 
                      int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
                      const float4* geom, const float* x, float* m, cudaStream_t st) {
     const int lm = L.conv.lmax;
+    const bool bf = prec == SEVENNET_BF16;
+    // BF16: the tensor-core contraction (conv_fwd_tc.cu) where the block allows
+    // it; its cp.async staging wants 16-byte aligned x rows
+    if (bf && L.conv.tc_ok && (reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+        launch_conv_fwd_tc(L, H, n_atoms, n_edges, row_ptr, dst, src, geom, x, m, st);
+        return;
+    }
     const int grid = conv_grid(n_atoms, conv_ctas_per_sm(lm));
     const size_t sm = smem_bytes(L.conv, H, false, prec == SEVENNET_BF16);
-    const bool bf = prec == SEVENNET_BF16;
 #define SN_LF(HH, BB, LL) conv_fwd_kernel<HH, BB, LL><<<grid, CONV_THREADS, sm, st>>>(             \
         L.conv, L.mlp0, L.mlp1, L.mlp2, L.mlp2h, L.mlp1Th, (int)n_atoms, (int)n_edges, row_ptr, dst, src, geom, x, m)
     if (H == 64) {

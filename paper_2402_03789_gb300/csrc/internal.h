@@ -166,6 +166,33 @@ __host__ __device__ constexpr bool fwd_cpl_compiled(int H, int l1, int nacc, int
     return cpl == 1 || (H == 64 && cpl * (2 * l1 + 1) <= 6 && cpl * nacc <= 20);
 }
 
+// Tensor-core forward (BF16 path): the contraction over (edge, m1) runs on
+// mma.m16n8k16 with 16 channels as M, m3 as N and K = 16 slots holding
+// (edge, m1) pairs of edges that share a receiver.  EG edges fill one K group:
+// 16 for l1 = 0, 4 for l1 = 1 (3 slots each, one padding), 2 for l1 = 2, 3
+// (two lanes of 4 slots per edge).  The paths of one input irrep are split
+// into sets of at most 24 / (16 / EG) paths; a work unit is one set over 16
+// channels.
+__host__ __device__ constexpr int tc_eg(int n1) { return n1 == 1 ? 16 : (n1 == 3 ? 4 : 2); }
+__host__ __device__ constexpr int tc_nkg(int n1) { return EC / tc_eg(n1); }
+__host__ __device__ constexpr int tc_set_cap(int n1) { return 24 / tc_nkg(n1); }
+constexpr int TC_MAX_SETS = 6;
+constexpr int MAX_SLOTS_TC = 24;
+
+__host__ __device__ constexpr PathSets tc_path_sets(int l1, int lmax, int kind) {
+    PathSets s{0, {0, 0, 0, 0, 0, 0, 0}};
+    const PathList p = path_list(l1, lmax, kind);
+    if (p.n == 0) return s;
+    const int cap = tc_set_cap(2 * l1 + 1);
+    int n = 0;
+    for (int i = 0; i < p.n; ++i) {
+        if (n == cap) { s.b[++s.n] = i; n = 0; }
+        ++n;
+    }
+    s.b[++s.n] = p.n;
+    return s;
+}
+
 struct PathDesc {
     int32_t l1, l2, l3, kind;
     int32_t mul;      // channels of the path (= multiplicity of l1 in the block input)
@@ -175,6 +202,7 @@ struct PathDesc {
     int32_t m_mul;    // channels of the l3 message block
     int32_t m_ch0;    // first channel of this path inside the l3 block
     int32_t g_off;    // offset of this path's G matrix in the per-edge buffer
+    int32_t b_off;    // tensor-core forward: first 32-bit word of the path's B fragments in shared memory
 };
 
 // Everything a convolution kernel needs to know about one block.
@@ -201,6 +229,14 @@ struct ConvDesc {
     int16_t n_slots[CONV_WARPS];
     int16_t slot_group[CONV_WARPS][MAX_SLOTS];  // (l1 << 11) | (set << 8) | (channel block << 2) | log2 CPL
     int32_t WpadB;      // row stride (BF16 values) of the BF16 weight tile: rows start on 16 bytes
+    // tensor-core forward (BF16): work units, B-fragment words, staged x rows
+    int16_t n_slots_tc[CONV_WARPS];
+    int16_t slot_tc[CONV_WARPS][MAX_SLOTS_TC];  // (l1 << 12) | (set << 8) | 16-channel tile
+    int32_t nBF;                  // 32-bit words of B fragments per chunk
+    int32_t xs_off[NL];           // floats: staged x region of irrep l1 (EC rows)
+    int32_t xs_stride[NL];        // floats between the staged rows of two edges
+    int32_t xs_total;             // floats of the staged x regions
+    int32_t tc_ok;                // 1: the block can run the tensor-core forward
 };
 
 // One row-block matrix product of a per-irrep linear: rows are (atom, m)
@@ -377,6 +413,12 @@ void launch_conv_bwd(const LayerDev& L, int H, sevennet_precision prec, int64_t 
                      const float4* geom, const float* x, const float* gm, float* gx,
                      float* gd, cudaStream_t st);
 sevennet_status conv_configure(int H, const std::vector<LayerDev>& layers);
+// tensor-core forward of the BF16 path (conv_fwd_tc.cu)
+size_t conv_tc_smem_bytes(const ConvDesc& D, int H);
+sevennet_status conv_configure_fwd_tc(int H, size_t need);
+void launch_conv_fwd_tc(const LayerDev& L, int H, int64_t n_atoms, int64_t n_edges, const int* row_ptr,
+                        const int* dst, const int* src, const float4* geom, const float* x, float* m,
+                        cudaStream_t st);
 void launch_gemm(const GemmBatch& b, sevennet_precision prec, cudaStream_t st);
 void launch_embed(const float* table, const int* species, int64_t n, int mul0, int n_species, float* h,
                   cudaStream_t st);

@@ -103,3 +103,30 @@ def test_conv_adjoint_matches_finite_differences():
         xm = xg.detach().clone(); xm[v, j] -= h
         fd = (loss(d0.detach(), xp) - loss(d0.detach(), xm)) / (2 * h)
         assert abs(fd - gx[v, j]) <= 2e-3 * scale_x, (v, j, fd, gx[v, j])
+
+
+@pytest.mark.parametrize("spec,layer", [(MODEL_SEVENNET0, 0), (MODEL_SEVENNET0, 2), (MODEL_SEVENNET0, 4),
+                                        (MODEL_TINY, 1)])
+def test_bf16_conv_forward_matches_oracle(spec, layer):
+    # BF16 path: w, x and the G matrices enter the tensor cores as BF16 with FP32
+    # accumulation; the messages stay within a few BF16 roundings of the FP64 oracle
+    model = get_model(spec)
+    s, dst, src, d, row_ptr, L, x = _setup(spec, layer, seed=43)
+    n = s.n_atoms
+    Wd = ModelLayout(spec).unpack(normal_weights(oracle.n_params(spec)))
+    dt = torch.tensor(d)
+    Y, B = edge_features(spec, dt)
+    w = radial_mlp(spec, Wd, layer, B)
+    m = conv_layer(spec, L, {l: torch.tensor(v) for l, v in x.items()}, Y, w,
+                   torch.as_tensor(dst), torch.as_tensor(src), n)
+    mo = torch.cat([m[l].reshape(n, -1) for l in sorted(m)], dim=1).numpy()
+    dev = "cuda"
+    mg = model.conv_forward(layer, torch.tensor(row_ptr, dtype=torch.int32, device=dev),
+                            torch.tensor(src, dtype=torch.int32, device=dev),
+                            torch.tensor(d, dtype=torch.float32, device=dev),
+                            torch.tensor(_pack(x, n), dtype=torch.float32, device=dev), "bf16")
+    mg = mg.cpu().numpy()
+    rel = np.linalg.norm(mg - mo) / np.linalg.norm(mo)
+    worst = np.abs(mg - mo).max() / np.abs(mo).max()
+    print(f"bf16 layer {layer}: messages rel {rel:.2e}, max {worst:.2e}")
+    assert rel <= 1e-2 and worst <= 3e-2
