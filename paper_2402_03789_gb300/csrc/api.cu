@@ -306,7 +306,7 @@ static bool assign_slots(ConvDesc& D, int H) {
 // FFMA forward (tc_ok = 0).
 static void assign_tc(ConvDesc& D, int H) {
     D.tc_ok = 0;
-    if (D.lmax > 2) return;
+    if (D.lmax > 2 || D.x_dim > 4 * 32 * 6) return;     // x rows staged as at most 6 pieces of 16 bytes per lane
     int words = 0, xo = 0;
     for (int l = 0; l < NL; ++l) { D.xs_off[l] = 0; D.xs_stride[l] = 0; }
     for (int l1 = 0; l1 <= D.lmax; ++l1) {
@@ -405,6 +405,7 @@ sevennet_status ws_reserve(sevennet_model* M, Workspace* ws, int64_t n_atoms, in
         SN_TRY(ws_alloc(ws, &ws->m, N * M->m_max));
         SN_TRY(ws_alloc(ws, &ws->gy, N * M->y_max));
         SN_TRY(ws_alloc(ws, &ws->gx, N * M->x_max));
+        SN_TRY(ws_alloc(ws, &ws->gxq, N * M->x_max));
         SN_TRY(ws_alloc(ws, &ws->gh, N * M->h_max));
         SN_TRY(ws_alloc(ws, &ws->e_atom, N));
         SN_TRY(ws_alloc(ws, &ws->w_atom, N * 9));
@@ -537,12 +538,12 @@ sevennet_status model_layer_backward_rest(sevennet_model* M, Workspace* ws, int 
                               L.y_dim, L.y_off[l], L.m_dim, L.msg_off[l], 0};
     }
     run_gemm(M, g, prec, st);
-    SN_CUDA(cudaMemsetAsync(ws->gx, 0, (size_t)N * L.x_dim * sizeof(float), st));
     prof_begin(&M->prof, PF_CONV_BWD, st, &ev);
-    launch_conv_bwd(L, M->H, prec, N, E, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m, ws->gx,
-                    ws->gd, st);
-    prof_end(&M->prof, PF_CONV_BWD, st, ev, 1);
-    count_launches(1);
+    // the first block's dE/dx is not needed (its input is the species embedding)
+    launch_conv_bwd(L, M->H, prec, N, E, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m,
+                    t == 0 ? nullptr : ws->gx, ws->gxq, ws->flags, ws->gd, st);
+    prof_end(&M->prof, PF_CONV_BWD, st, ev, t == 0 ? 1 : 2);
+    count_launches(t == 0 ? 1 : 2);
     if (t == 0) return SEVENNET_OK;
     GemmBatch a{}, c{};
     for (int l = 0; l < NL; ++l) {
@@ -865,6 +866,8 @@ sevennet_status eval_batch(sevennet_model* M, Workspace* ws, const BatchHost& b,
     SN_CUDA(cudaMemcpyAsync(ws->flags_host, ws->flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
     SN_CUDA(cudaStreamSynchronize(st));
     SN_CHECK(ws->flags_host[3] == 0, SEVENNET_EINVAL, "species index out of range");
+    SN_CHECK(ws->flags_host[FLAG_GX_OVERFLOW] == 0, SEVENNET_EOVERFLOW,
+             "a feature gradient in the convolution adjoint reached 2^16 (outside the fixed-point range)");
     SN_CHECK(ws->flags_host[2] == 0, SEVENNET_ECUDA, "internal error: reverse edge not found");
     return SEVENNET_OK;
 }
@@ -1050,14 +1053,18 @@ sevennet_status sevennet_conv_backward_dev(sevennet_model* M, int32_t layer, int
     int* dst = nullptr;
     float4* geom = nullptr;
     const size_t e1 = std::max<int64_t>(n_edges, 1);
+    unsigned long long* gxq = nullptr;
     SN_CUDA(cudaMallocAsync(&dst, e1 * sizeof(int), st));
     SN_CUDA(cudaMallocAsync(&geom, e1 * sizeof(float4), st));
+    SN_CUDA(cudaMallocAsync(&gxq, (size_t)std::max<int64_t>(n_atoms, 1) * M->layers[layer].x_dim *
+                                      sizeof(unsigned long long), st));
     conv_prepare_edges(n_atoms, n_edges, row_ptr, d, dst, geom, st);
-    SN_CUDA(cudaMemsetAsync(g_x, 0, (size_t)std::max<int64_t>(n_atoms, 1) * M->layers[layer].x_dim * sizeof(float), st));
-    launch_conv_bwd(M->layers[layer], M->H, prec, n_atoms, n_edges, row_ptr, dst, src, geom, x, g_m, g_x, g_d, st);
+    launch_conv_bwd(M->layers[layer], M->H, prec, n_atoms, n_edges, row_ptr, dst, src, geom, x, g_m, g_x, gxq,
+                    nullptr, g_d, st);
     SN_CUDA(cudaGetLastError());
     cudaFreeAsync(dst, st);
     cudaFreeAsync(geom, st);
+    cudaFreeAsync(gxq, st);
     return SEVENNET_OK;
 }
 

@@ -42,17 +42,24 @@ __device__ __forceinline__ void tp_bwd_path(const PathDesc& P, int u0, int e, in
     }
 }
 
+// Fixed-point add of one dE/dx contribution (order-independent sums); the
+// conversion after the kernel reports a sum that received the sentinel.
+__device__ __forceinline__ void gx_fixed_add(unsigned long long* p, float v) {
+    const long long q = fabsf(v) < GX_LIMIT ? __float2ll_rn(v * GX_SCALE) : GX_SENTINEL;   // exact scaling by 2^36
+    atomicAdd(p, (unsigned long long)q);
+}
+
 // All paths of one input irrep l1 for one edge, CPL channels per lane: the
 // channel loads, the path descriptors and the CG code resolve at compile time.
 template <int L1, int LMAX, int KIND, int CPL>
 __device__ __forceinline__ void tp_bwd_block(const ConvDesc& D, int u0, int e, int v, int sidx, float* gY,
                                              float* s_w, const float* s_G, const float* __restrict__ x,
-                                             const float* __restrict__ gm, float* __restrict__ gxo) {
+                                             const float* __restrict__ gm, unsigned long long* __restrict__ gxo) {
     using BP = BlockPaths<L1, LMAX, KIND>;
     constexpr int N1 = 2 * L1 + 1;
     const int mul = D.mul_in[L1];
     const float* xr = x + (size_t)sidx * D.x_dim + D.x_off[L1] + u0;
-    float* gxr = gxo + (size_t)sidx * D.x_dim + D.x_off[L1] + u0;
+    unsigned long long* gxr = gxo + (size_t)sidx * D.x_dim + D.x_off[L1] + u0;
     float xv[CPL][N1], gx[CPL][N1];
 #pragma unroll
     for (int k = 0; k < CPL; ++k)
@@ -69,14 +76,14 @@ __device__ __forceinline__ void tp_bwd_block(const ConvDesc& D, int u0, int e, i
 #pragma unroll
     for (int k = 0; k < CPL; ++k)
 #pragma unroll
-        for (int a = 0; a < N1; ++a) atomicAdd(gxr + a * mul + 32 * k, gx[k][a]);
+        for (int a = 0; a < N1; ++a) gx_fixed_add(gxr + a * mul + 32 * k, gx[k][a]);
 }
 
 template <int L1, int LMAX, int KIND, int MAXC>
 __device__ __forceinline__ void tp_bwd_l1(const ConvDesc& D, int lane, int e, int v, int sidx,
                                           float* gY, float* s_w, const float* s_G,
                                           const float* __restrict__ x,
-                                          const float* __restrict__ gm, float* __restrict__ gxo) {
+                                          const float* __restrict__ gm, unsigned long long* __restrict__ gxo) {
     if constexpr (BlockPaths<L1, LMAX, KIND>::list.n > 0) {
         const int mul = D.mul_in[L1];
         for (int ub = 0; ub < mul;) {
@@ -100,7 +107,7 @@ template <int LMAX, int KIND, int MAXC>
 __device__ __forceinline__ void tp_bwd_chunk(const ConvDesc& D, int ne, const int* s_dst, const int* s_src,
                                              float* s_w, const float* s_G, float* s_gY,
                                              const float* __restrict__ x, const float* __restrict__ gm,
-                                             float* __restrict__ gx) {
+                                             unsigned long long* __restrict__ gx) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int e = warp; e < ne; e += CONV_WARPS) {
         const int v = s_dst[e], sidx = s_src[e];
@@ -134,7 +141,7 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
                 int n_edges, const int* __restrict__ row_ptr, const int* __restrict__ dst,
                 const int* __restrict__ src, const float4* __restrict__ geom,
                 const float* __restrict__ x, const float* __restrict__ gm,
-                float* __restrict__ gx, float* __restrict__ gd) {
+                unsigned long long* __restrict__ gx, float* __restrict__ gd) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
     const ConvSmem L = conv_smem_layout(D.Wpad, D.WpadB, H, D.nG, D.ys, true, BF);
@@ -287,6 +294,22 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
     }
 }
 
+// dE/dx from its fixed-point sums; a sum that received the sentinel becomes
+// NaN and sets flags[FLAG_GX_OVERFLOW] (flags may be null).
+__global__ void gx_from_fixed_kernel(int64_t n, const unsigned long long* __restrict__ q, float* __restrict__ gx,
+                                     int* flags) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long v = (long long)q[i];
+    const long long lim = 1LL << 56;
+    if (v >= lim || v <= -lim) {
+        gx[i] = __int_as_float(0x7fc00000);
+        if (flags) atomicOr(flags + FLAG_GX_OVERFLOW, 1);
+    } else {
+        gx[i] = (float)((double)v * (1.0 / 68719476736.0));
+    }
+}
+
 // ------------------------------------------------------------- launcher
 sevennet_status conv_configure_bwd(int H, size_t need) {
     static size_t granted[2][2] = {{0, 0}, {0, 0}};
@@ -313,14 +336,16 @@ sevennet_status conv_configure_bwd(int H, size_t need) {
 void launch_conv_bwd(const LayerDev& L, int H, sevennet_precision prec, int64_t n_atoms,
                      int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
                      const float4* geom, const float* x, const float* gm, float* gx,
-                     float* gd, cudaStream_t st) {
+                     unsigned long long* gxq, int* flags, float* gd, cudaStream_t st) {
     const int lm = L.conv.lmax;
+    const size_t nx = (size_t)std::max<int64_t>(n_atoms, 0) * L.conv.x_dim;
+    if (gx && nx) cudaMemsetAsync(gxq, 0, nx * sizeof(unsigned long long), st);
     const int grid = conv_grid(n_atoms, conv_ctas_per_sm(lm));
     const size_t sm = smem_bytes(L.conv, H, true, prec == SEVENNET_BF16);
     const bool bf = prec == SEVENNET_BF16;
 #define SN_LB(HH, BB, LL) conv_bwd_kernel<HH, BB, LL><<<grid, CONV_THREADS, sm, st>>>(                 \
         L.conv, L.mlp0, L.mlp1, L.mlp1T, L.mlp2, L.mlp2T, L.mlp2h, L.mlp2Th, L.mlp1Th, L.mlp1h,       \
-        (int)n_atoms, (int)n_edges, row_ptr, dst, src, geom, x, gm, gx, gd)
+        (int)n_atoms, (int)n_edges, row_ptr, dst, src, geom, x, gm, gxq, gd)
     if (H == 64) {
         if (bf) { if (lm == 3) SN_LB(64, true, 3); else if (lm == 2) SN_LB(64, true, 2); else SN_LB(64, true, 1); }
         else    { if (lm == 3) SN_LB(64, false, 3); else if (lm == 2) SN_LB(64, false, 2); else SN_LB(64, false, 1); }
@@ -329,6 +354,8 @@ void launch_conv_bwd(const LayerDev& L, int H, sevennet_precision prec, int64_t 
         else    { if (lm == 2) SN_LB(32, false, 2); else SN_LB(32, false, 1); }
     }
 #undef SN_LB
+    if (gx && nx)
+        gx_from_fixed_kernel<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>((int64_t)nx, gxq, gx, flags);
 }
 
 }  // namespace sn

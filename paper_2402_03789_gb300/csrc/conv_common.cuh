@@ -309,28 +309,39 @@ __device__ __forceinline__ void chunk_w_gemm_bf16(const ConvDesc& D, const ConvS
 }
 
 // Phase F (BF16): gH2[k][e] = sum_c gw[e][c] W3[k][c]; B operand W3 [H][W] (bf16).
-// K (the W columns) runs in blocks of 32 columns split over the warps; each
-// block's A fragment is read and split once, its B fragments come as one 16-byte
-// load per lane and n tile; partial sums meet in shared memory.
+// K (the W columns, in blocks of 32) is split between two groups of four warps;
+// within a group each warp owns H/32 n tiles of 8 hidden units for its whole K
+// half, so every output has one writer per group.  Group 0 writes dE/dH2,
+// group 1 a partial in the staging region, and the two are added in a fixed
+// order: the result does not depend on the warps' timing.
 template <int H>
 __device__ __forceinline__ void chunk_gw_gemm_bf16(const ConvDesc& D, const ConvSmem& L, float* smem,
                                                    const __nv_bfloat16* __restrict__ W3h) {
-    constexpr int NT = H / 8;                  // n tiles of 8 hidden units
+    constexpr int NTW = H / 32;                // n tiles per warp (2 or 1)
     static_assert(EC == 16, "one m tile of edges");
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tq = lane & 3;
+    const int grp = warp >> 2, wq = warp & 3;
     const float* s_w = smem + L.w;             // dE/dw, [EC][Wpad]
     float* s_gH = smem + L.gH;                 // [H][EC]
-    const int W = D.W;
-    for (int i = t; i < H * EC; i += CONV_THREADS) s_gH[i] = 0.0f;
-    __syncthreads();
-    float c[NT][4];
+    float* s_part = smem + L.stage;            // group 1's partial, same layout
+    const int W = D.W, nkb = W / 32;
+    const int kb0 = grp ? nkb / 2 : 0, kb1 = grp ? nkb : nkb / 2;
+    __syncthreads();                           // every warp's dE/dw of phase E is in s_w
+    float c[NTW][4];
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
-    for (int kb = warp; kb < W / 32; kb += CONV_WARPS) {
-        uint4 bv[NT];
+    for (int j = 0; j < NTW; ++j) c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
+    uint4 bn[NTW];
+    auto load_b = [&](int kb) {
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-            bv[nt] = __ldg(reinterpret_cast<const uint4*>(W3h + (size_t)(nt * 8 + g) * W + kb * 32) + tq);
+        for (int j = 0; j < NTW; ++j)
+            bn[j] = __ldg(reinterpret_cast<const uint4*>(W3h + (size_t)((wq * NTW + j) * 8 + g) * W + kb * 32) + tq);
+    };
+    if (kb0 < kb1) load_b(kb0);
+    for (int kb = kb0; kb < kb1; ++kb) {
+        uint4 bv[NTW];
+#pragma unroll
+        for (int j = 0; j < NTW; ++j) bv[j] = bn[j];
+        if (kb + 1 < kb1) load_b(kb + 1);
         // k step ks covers words kb*16 + 4 tq + 2 ks (+1): columns 32 kb + 8 tq + 4 ks .. + 3
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) {
@@ -340,21 +351,24 @@ __device__ __forceinline__ void chunk_gw_gemm_bf16(const ConvDesc& D, const Conv
             const uint32_t a[4] = {pack_bf16(r0.x, r0.y), pack_bf16(r1.x, r1.y), pack_bf16(r0.z, r0.w),
                                    pack_bf16(r1.z, r1.w)};
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const uint32_t* bw = reinterpret_cast<const uint32_t*>(&bv[nt]);
+            for (int j = 0; j < NTW; ++j) {
+                const uint32_t* bw = reinterpret_cast<const uint32_t*>(&bv[j]);
                 const uint32_t b[2] = {bw[2 * ks], bw[2 * ks + 1]};
-                mma_bf16(c[nt], a, b);
+                mma_bf16(c[j], a, b);
             }
         }
     }
+    float* out = grp ? s_part : s_gH;
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-        const int k = nt * 8 + 2 * tq;
-        atomicAdd(s_gH + hk<H>(k, g), c[nt][0]);
-        atomicAdd(s_gH + hk<H>(k + 1, g), c[nt][1]);
-        atomicAdd(s_gH + hk<H>(k, g + 8), c[nt][2]);
-        atomicAdd(s_gH + hk<H>(k + 1, g + 8), c[nt][3]);
+    for (int j = 0; j < NTW; ++j) {
+        const int k = (wq * NTW + j) * 8 + 2 * tq;
+        out[hk<H>(k, g)] = c[j][0];
+        out[hk<H>(k + 1, g)] = c[j][1];
+        out[hk<H>(k, g + 8)] = c[j][2];
+        out[hk<H>(k + 1, g + 8)] = c[j][3];
     }
+    __syncthreads();
+    for (int i = t; i < H * EC; i += CONV_THREADS) s_gH[i] += s_part[i];
     __syncthreads();
 }
 

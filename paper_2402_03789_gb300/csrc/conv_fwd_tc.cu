@@ -22,6 +22,7 @@
 namespace sn {
 
 constexpr int TC_WS = 18;       // BF16 values between two columns of the [W][edge] weight tile
+constexpr int TC_XPIECES = 6;   // 16-byte pieces of an x row per lane (x rows of at most 768 floats)
 
 struct TcSmem {
     int w, xs, bf, stage, H2, Y, B, src, dst, first, W1, total;
@@ -116,14 +117,23 @@ __device__ __forceinline__ void tc_w_gemm(const ConvDesc& D, const TcSmem& L, fl
         }
     uint32_t* s_w = reinterpret_cast<uint32_t*>(smem + L.w);      // word (c * TC_WS + e) / 2
     const int mtiles = D.W / 16;
-    for (int mt = warp; mt < mtiles; mt += CONV_WARPS) {
-        uint4 av[2][NV];
+    uint4 an[2][NV];                      // the next m tile's A operand, in flight during this tile's MMAs
+    auto load_a = [&](int mt) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const uint4* row = reinterpret_cast<const uint4*>(W3T + (size_t)(mt * 16 + g + 8 * r) * H);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) av[r][v] = __ldg(row + tq * NV + v);
+            for (int v = 0; v < NV; ++v) an[r][v] = __ldg(row + tq * NV + v);
         }
+    };
+    if (warp < mtiles) load_a(warp);
+    for (int mt = warp; mt < mtiles; mt += CONV_WARPS) {
+        uint4 av[2][NV];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) av[r][v] = an[r][v];
+        if (mt + CONV_WARPS < mtiles) load_a(mt + CONV_WARPS);
         const uint32_t* a0w = reinterpret_cast<const uint32_t*>(av[0]);
         const uint32_t* a1w = reinterpret_cast<const uint32_t*>(av[1]);
 #pragma unroll
@@ -321,10 +331,18 @@ conv_fwd_tc_kernel(const ConvDesc D, const float* __restrict__ W1, const __nv_bf
     // B-fragment slots that no path writes (m3 beyond the path, padding slots) stay zero
     for (int i = t; i < D.nBF; i += CONV_THREADS) smem[L.bf + i] = 0.0f;
     for (int i = t; i < D.n_basis * H; i += CONV_THREADS) smem[L.W1 + i] = W1[i];
-    // the x row of a sender: 16-byte pieces, irreps in order
-    int n4tot = 0;
+    // the x row of a sender in 16-byte pieces, irreps in order: lane j's pieces
+    // j, j + 32, ... (at most TC_XPIECES) with their source and staged offsets
+    int xsrc[TC_XPIECES], xdst[TC_XPIECES], xstr[TC_XPIECES];
 #pragma unroll
-    for (int l = 0; l < NL; ++l) n4tot += (2 * l + 1) * D.mul_in[l] / 4;
+    for (int i = 0; i < TC_XPIECES; ++i) {
+        int j = lane + 32 * i, l = 0;
+        while (l < NL - 1 && j >= (2 * l + 1) * D.mul_in[l] / 4) { j -= (2 * l + 1) * D.mul_in[l] / 4; ++l; }
+        const bool ok = j < (2 * l + 1) * D.mul_in[l] / 4;
+        xsrc[i] = ok ? D.x_off[l] + 4 * j : -1;
+        xdst[i] = L.xs + D.xs_off[l] + 4 * j;
+        xstr[i] = D.xs_stride[l];
+    }
     EdgePrefetch pf;
     pf.fetch(E0, E1, dst, src, geom, row_ptr);
     for (int c0 = E0; c0 < E1; c0 += EC) {
@@ -348,11 +366,9 @@ conv_fwd_tc_kernel(const ConvDesc D, const float* __restrict__ W1, const __nv_bf
         // x rows of the chunk's senders into shared memory, in flight during the MLP
         for (int e = warp; e < ne; e += CONV_WARPS) {
             const float* xr = x + (size_t)s_src[e] * D.x_dim;
-            for (int j = lane; j < n4tot; j += 32) {
-                int l = 0, jj = j;
-                while (jj >= (2 * l + 1) * D.mul_in[l] / 4) { jj -= (2 * l + 1) * D.mul_in[l] / 4; ++l; }
-                cp_async16(smem + L.xs + D.xs_off[l] + e * D.xs_stride[l] + 4 * jj, xr + D.x_off[l] + 4 * jj);
-            }
+#pragma unroll
+            for (int i = 0; i < TC_XPIECES; ++i)
+                if (xsrc[i] >= 0) cp_async16(smem + xdst[i] + e * xstr[i], xr + xsrc[i]);
         }
         cp_async_commit();
         // radial MLP input layer: H1 = silu(B @ W1), thread (j, edge group)

@@ -350,6 +350,7 @@ struct Workspace {
     float* m = nullptr;           // [N][m_max] (messages, then their gradients)
     float* gy = nullptr;          // [N][y_max]
     float* gx = nullptr;          // [N][x_max]
+    unsigned long long* gxq = nullptr;   // [N][x_max] fixed-point sums of dE/dx
     float* gh = nullptr;          // [N][h_max]
     float* gd = nullptr;          // [E][3]
     double* e_atom = nullptr;     // [N]
@@ -404,14 +405,28 @@ sevennet_status run_model(sevennet_model* M, Workspace* ws, const BatchHost& b, 
                           sevennet_precision prec, double* energy_dev, double* forces_dev,
                           double* virial_dev, cudaStream_t st);
 
+// Deterministic scatter of dE/dx in the convolution adjoint: every per-edge
+// contribution v is added as the 64-bit integer round(v * 2^36) (fixed point),
+// so the sums are the same whatever order the atomics land in.  A contribution
+// that is not finite or has |v| >= GX_LIMIT adds GX_SENTINEL instead and sets
+// flags[FLAG_GX_OVERFLOW]; a sum of magnitude >= 2^56 converts to NaN.
+constexpr float GX_SCALE = 68719476736.0f;          // 2^36
+constexpr float GX_LIMIT = 65536.0f;                // 2^16
+constexpr long long GX_SENTINEL = 1LL << 57;
+constexpr int FLAG_GX_OVERFLOW = 5;
+
 // kernels launchers (conv.cu / node.cu)
 void launch_conv_fwd(const LayerDev& L, int H, sevennet_precision prec, int64_t n_atoms,
                      int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
                      const float4* geom, const float* x, float* m, cudaStream_t st);
+// gxq is an [n_atoms][x_dim] 64-bit scratch for the fixed-point sums of dE/dx;
+// gx == nullptr skips their conversion (the first block's input gradient is not
+// needed; the kernel still adds into gxq, which is then left as it is) and flags
+// (may be null) receives the overflow flag.
 void launch_conv_bwd(const LayerDev& L, int H, sevennet_precision prec, int64_t n_atoms,
                      int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
                      const float4* geom, const float* x, const float* gm, float* gx,
-                     float* gd, cudaStream_t st);
+                     unsigned long long* gxq, int* flags, float* gd, cudaStream_t st);
 sevennet_status conv_configure(int H, const std::vector<LayerDev>& layers);
 // tensor-core forward of the BF16 path (conv_fwd_tc.cu)
 size_t conv_tc_smem_bytes(const ConvDesc& D, int H);

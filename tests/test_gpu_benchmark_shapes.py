@@ -25,7 +25,10 @@ def test_benchmark_shape_matches_oracle(n_layers, channels, lmax):
     assert e_pa <= 1e-6 and f_rel <= 1e-5 and w_rel <= 1e-5, (e_pa, f_rel, w_rel)
     E, F, W = model.evaluate(s.pos, s.cell, s.species, "bf16")
     e_pa, f_rel, w_rel = errors(E, F, W, Eo, Fo, Wo, s.n_atoms)
-    assert f_rel <= 5e-3, (e_pa, f_rel, w_rel)
+    print(f"bf16 {n_layers}x{channels} lmax {lmax}: |dE|/N={e_pa:.2e} F={f_rel:.2e} W={w_rel:.2e}")
+    # energy and virial bounds from the measured errors of these shapes (at most
+    # 6.1e-6 eV/atom and 3.4e-3) with a margin of about 3x
+    assert f_rel <= 5e-3 and e_pa <= 2e-5 and w_rel <= 1e-2, (e_pa, f_rel, w_rel)
 
 
 @pytest.mark.parametrize("n_layers,channels,lmax", [(2, 4, 3), (3, 8, 3), (3, 16, 2)])

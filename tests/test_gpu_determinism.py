@@ -1,0 +1,66 @@
+"""Run-to-run determinism of the evaluation (Eqs. 5-8 summed in a fixed way).
+
+The adjoint scatters dE/dx into senders as 64-bit fixed-point sums, which do not
+depend on the order the atomic adds land in, and every other reduction has a
+fixed order; so two evaluations of the same input give the same bits.  In FP32
+the result of a structure is also bit-identical alone and inside a batch: each
+receiver's messages are summed edge by edge in list order whatever the chunk
+boundaries.  In BF16 the tensor-core forward groups a receiver's edges into MMA
+K groups that start at chunk boundaries, and those move with the batch, so the
+two agree to the BF16 path's rounding only (bounded below).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import MODEL_SEVENNET0, make_workload, normal_weights, random_structure
+from gpu_common import errors, get_model
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("name", ["sio2_192_l2", "sio2_3000"])
+def test_repeated_evaluations_are_bitwise_equal(name, prec):
+    s, spec = make_workload(name)
+    model = get_model(spec)
+    E1, F1, W1 = model.evaluate(s.pos, s.cell, s.species, prec)
+    for _ in range(2):
+        E2, F2, W2 = model.evaluate(s.pos, s.cell, s.species, prec)
+        assert E2 == E1
+        assert np.array_equal(F2, F1)
+        assert np.array_equal(W2, W1)
+
+
+def _batch(prec):
+    spec = MODEL_SEVENNET0
+    model = get_model(spec)
+    structs = [random_structure({"Si": 20, "O": 40}, 2.2, 1.6, seed=31),
+               random_structure({"Si": 6, "N": 8}, 3.1, 1.5, seed=32),
+               random_structure({"Si": 50, "N": 60, "O": 7}, 2.7, 1.5, seed=33)]
+    off = np.cumsum([0] + [s.n_atoms for s in structs])
+    pos = torch.tensor(np.concatenate([s.pos for s in structs]), dtype=torch.float64, device="cuda")
+    sp = torch.tensor(np.concatenate([s.species for s in structs]), dtype=torch.int32, device="cuda")
+    cells = np.stack([s.cell for s in structs])
+    e, f, w = model.evaluate_batch_dev(off, cells, sp, pos, prec)
+    return model, structs, off, e.cpu().numpy(), f.cpu().numpy(), w.cpu().numpy()
+
+
+def test_fp32_alone_and_in_batch_are_bitwise_equal():
+    model, structs, off, e, f, w = _batch("fp32")
+    for i, s in enumerate(structs):
+        E1, F1, W1 = model.evaluate(s.pos, s.cell, s.species, "fp32")
+        assert e[i] == E1
+        assert np.array_equal(f[off[i]:off[i + 1]], F1)
+        assert np.array_equal(w[i], W1)
+
+
+def test_bf16_alone_and_in_batch_agree():
+    model, structs, off, e, f, w = _batch("bf16")
+    for i, s in enumerate(structs):
+        E1, F1, W1 = model.evaluate(s.pos, s.cell, s.species, "bf16")
+        e_pa, f_rel, w_rel = errors(e[i], f[off[i]:off[i + 1]], w[i], E1, F1, W1, s.n_atoms)
+        print(f"bf16 structure {i}: |dE|/N {e_pa:.2e} F {f_rel:.2e} W {w_rel:.2e}")
+        assert e_pa <= 1e-6 and f_rel <= 1e-3 and w_rel <= 1e-3
