@@ -229,6 +229,8 @@ def serving_run(sn, model, precision, n_requests=512, rate_hz=200.0, budget_gb=8
 
     Requests are submitted at their arrival times; latency = completion - arrival
     on the server clock.  Returns p50/p99 latency, throughput and batching stats.
+    At an offered rate above the server's capacity the queue fills and the
+    throughput is the server's own (saturated).
     """
     from synth import serving_trace
     trace = serving_trace(n_requests, rate_hz, seed=6)
@@ -272,6 +274,38 @@ def serving_run(sn, model, precision, n_requests=512, rate_hz=200.0, budget_gb=8
 
 # initial-velocity seeds of the MD workloads (3000 K)
 MD_VEL_SEED = {"sio2_3000": 3, "si3n4_112000": 8}
+
+
+def md_leg(sn, model, workload, precision, steps, warmup=3, device=0):
+    """NVE MD of one workload through sevennet_md_step (1 fs, Maxwell-Boltzmann
+    velocities at 3000 K): atom-steps/s by the host clock around one md_step call
+    of `steps` steps (one host synchronisation per call), and the drift of the
+    total energy."""
+    import numpy as np
+    import torch
+    from synth import make_workload, maxwell_boltzmann
+    from synth.configs import MASSES_AMU
+    s, _ = make_workload(workload)
+    masses = np.asarray(MASSES_AMU)
+    vel = maxwell_boltzmann(masses[s.species], 3000.0, seed=MD_VEL_SEED.get(workload, 3))
+    md = sn.MD(model, s.pos, vel, s.species, masses, s.cell, precision)
+    md.step(warmup, 1.0)
+    clk = ClockSampler(device)
+    torch.cuda.synchronize()
+    clk.start()
+    t0 = time.perf_counter()
+    ep, ek = md.step(steps, 1.0)
+    wall = time.perf_counter() - t0
+    clk.stop()
+    md.close()
+    etot = ep + ek
+    n = s.n_atoms
+    return {"workload": workload, "n_atoms": n, "precision": precision, "steps": steps, "warmup": warmup,
+            "dt_fs": 1.0, "ensemble": "NVE", "T_init_K": 3000.0,
+            "value": n * steps / wall, "unit": UNIT, "ms_per_step": wall * 1e3 / steps,
+            "etot_drift_eV_per_atom": float((etot[-1] - etot[0]) / n),
+            "etot_max_dev_eV_per_atom": float(np.max(np.abs(etot - etot[0])) / n),
+            "timing": "host wall clock around one sevennet_md_step call", "clocks": clk.summary()}
 
 
 def md_run(args, world, rank, dev, sn, model, s):
@@ -451,6 +485,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the other precision's line")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream measurement")
+    ap.add_argument("--no-md", action="store_true", help="skip the MD legs of the default run")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--md-steps", type=int, default=0, help="run MD for this many timed steps instead")
     ap.add_argument("--skin", type=float, default=0.0, help="MD: Verlet-list skin in A (0: rebuild every step)")
@@ -593,6 +628,13 @@ def main():
 
     if not args.no_serving and rank == 0:
         line["serving"] = serving_run(sn, model, args.precision)
+        # offered load far above capacity: the server's own throughput and latency, both precisions
+        line["serving_saturated"] = {p: serving_run(sn, model, p, rate_hz=20000.0) for p in ("bf16", "fp32")}
+
+    if not args.no_md and rank == 0 and args.workload == WORKLOAD:
+        # the MD configurations: 100 FP32 NVE steps of 3,000 atoms and 20 BF16 NVE steps of 112,000 atoms
+        line["md"] = {"sio2_3000_fp32": md_leg(sn, model, "sio2_3000", "fp32", 100, device=local),
+                      "si3n4_112000_bf16": md_leg(sn, model, "si3n4_112000", "bf16", 20, device=local)}
 
     if rank == 0 and world == 1 and not args.no_cpu:
         base, (s2, spec2, w2, res) = oracle_sample()

@@ -248,8 +248,13 @@ sevennet_status sevennet_md_create(sevennet_model* model, int64_t n_atoms,
                                    const double* cell, sevennet_precision prec,
                                    sevennet_md** out);
 /* Advance n_steps steps of dt_fs.  epot_log / ekin_log (host [n_steps] or
- * NULL) receive E_pot and E_kin after each step.  One synchronisation at the
- * end of the call. */
+ * NULL) receive E_pot and E_kin after each step.  The steps are enqueued
+ * without host synchronisation: neighbour lists keep their edge counts on the
+ * device, the Verlet-skin rebuild is decided on the device, and the call
+ * synchronises once, at the end.  If an edge list outgrew its preallocated
+ * capacity (reported by the device), the call restores the state it started
+ * from, enlarges the capacity and runs the steps again (a second
+ * synchronisation, rare); a second overflow returns EOVERFLOW. */
 sevennet_status sevennet_md_step(sevennet_md* md, int64_t n_steps, double dt_fs,
                                  double* epot_log, double* ekin_log);
 /* Host copies of the current state (each may be NULL). */
@@ -291,11 +296,17 @@ sevennet_status sevennet_md_get_stats(const sevennet_md* md, int64_t* n_builds, 
 void sevennet_md_destroy(sevennet_md* md);
 
 /* Serving: continuous batching of independent structures.  Requests are
- * copied at submission; a worker thread admits queued requests while the
- * predicted device bytes of the batches in flight stay within
- * hbm_budget_bytes, packs them into a batch and runs it on one of n_streams
- * streams, so batches overlap on the GPU and new arrivals join the next batch
- * without waiting for the running ones. */
+ * copied at submission.  At creation the HBM budget is split evenly over
+ * n_streams slots and each slot's workspace and pinned buffers are allocated
+ * for the atoms its share holds (about 47 KB per atom for SevenNet-0), so
+ * running a batch allocates and frees nothing and waits for nothing on the
+ * host.  A worker thread packs queued requests into a free slot (up to
+ * max_batch_structs structures and the slot's atoms), enqueues copy-in,
+ * neighbour build, evaluation and copy-out on the slot's stream, and retires
+ * batches by event; batches overlap on the GPU and new arrivals join the next
+ * batch without waiting for the running ones.  The results of a structure do
+ * not depend on the batch it ran in beyond FP summation order (bit-identical in
+ * FP32). */
 typedef struct {
     int64_t        n_atoms;
     const int32_t* species;   /* host [n_atoms] */
@@ -317,7 +328,8 @@ typedef struct {
 sevennet_status sevennet_server_create(sevennet_model* model, size_t hbm_budget_bytes,
                                        int32_t n_streams, int32_t max_batch_structs,
                                        sevennet_precision prec, sevennet_server** out);
-/* Queue a request; *ticket identifies it.  ENOMEM_ADMIT if it can never fit. */
+/* Queue a request; *ticket identifies it.  ENOMEM_ADMIT if it has more atoms
+ * than one slot holds (it could never run). */
 sevennet_status sevennet_server_submit(sevennet_server* s, const sevennet_request* req,
                                        uint64_t* ticket);
 /* Non-blocking: *done = 1 and the result copied (forces into res->forces) once

@@ -378,13 +378,16 @@ static sevennet_status ws_alloc(Workspace* ws, T** p, int64_t count) {
     return SEVENNET_OK;
 }
 
+// Grows the workspace to the given sizes.  Nothing happens (and nothing waits)
+// when the capacities suffice; a reallocation frees the old buffer first, and
+// cudaFree waits for the work that may still use it.
 sevennet_status ws_reserve(sevennet_model* M, Workspace* ws, int64_t n_atoms, int64_t n_edges,
                            int64_t n_bins, int64_t n_structs, cudaStream_t st) {
-    SN_CUDA(cudaStreamSynchronize(st));
+    (void)st;
     if (!ws->flags) {
-        SN_TRY(ws_alloc(ws, &ws->flags, 8));
+        SN_TRY(ws_alloc(ws, &ws->flags, FLAG_WORDS));
         void* hp = nullptr;
-        SN_CUDA(cudaMallocHost(&hp, 8 * sizeof(int)));
+        SN_CUDA(cudaMallocHost(&hp, FLAG_WORDS * sizeof(int)));
         ws->flags_host = static_cast<int*>(hp);
     }
     if (n_atoms > ws->cap_atoms) {
@@ -568,8 +571,9 @@ sevennet_status run_model(sevennet_model* M, Workspace* ws, const BatchHost& b, 
     model_embed(M, ws, N, st);
     for (int t = 0; t < T; ++t) model_layer_forward(M, ws, t, N, E, prec, st);
     model_readout(M, ws, N, st);
-    // reverse path
-    if (E > 0) SN_CUDA(cudaMemsetAsync(ws->gd, 0, (size_t)E * 3 * sizeof(float), st));
+    // reverse path (E < 0: the edge count is on the device; clear the capacity)
+    const int64_t E_clear = E < 0 ? ws->cap_edges : E;
+    if (E_clear > 0) SN_CUDA(cudaMemsetAsync(ws->gd, 0, (size_t)E_clear * 3 * sizeof(float), st));
     for (int t = T - 1; t >= 0; --t) {
         model_layer_backward_gate(M, ws, t, N, st);
         SN_TRY(model_layer_backward_rest(M, ws, t, N, E, prec, st));
@@ -845,30 +849,70 @@ __global__ void check_species_kernel(int64_t n, const int32_t* __restrict__ sp, 
     if (i < n && (sp[i] < 0 || sp[i] >= ns)) atomicOr(flags + 3, 1);
 }
 
-// Evaluate a batch whose positions and species are already on the device.
+// Enqueue the evaluation of a batch whose positions and species are on the
+// device: neighbour build and model with the edge count kept on the device
+// (no host synchronisation).  The edge capacity must have been reserved and the
+// flags cleared; check_flags reads the outcome once the stream has reached it.
+sevennet_status eval_enqueue(sevennet_model* M, Workspace* ws, const BatchHost& b,
+                             const int32_t* species_dev, const double* pos_dev, sevennet_precision prec,
+                             double* energy_dev, double* forces_dev, double* virial_dev, cudaStream_t st) {
+    const int64_t N = b.atom_off[b.n_structs];
+    int64_t E = -1;
+    cudaEvent_t ev;
+    prof_begin(&M->prof, PF_NEIGHBORS, st, &ev);
+    SN_TRY(build_neighbors(M, ws, b, pos_dev, species_dev, st, &E, 0.0, nullptr, true));
+    prof_end(&M->prof, PF_NEIGHBORS, st, ev, 10);
+    count_launches(10);
+    if (N > 0) {
+        check_species_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, species_dev, M->cfg.n_species,
+                                                                          ws->flags);
+        count_launches(1);
+    }
+    return run_model(M, ws, b, E, prec, energy_dev, forces_dev, virial_dev, st);
+}
+
+sevennet_status check_flags(const int* f) {
+    SN_CHECK(f[1] == 0, SEVENNET_EINVAL, "two atoms closer than 1e-8 A");
+    SN_CHECK(f[3] == 0, SEVENNET_EINVAL, "species index out of range");
+    SN_CHECK(f[FLAG_GX_OVERFLOW] == 0, SEVENNET_EOVERFLOW,
+             "a feature gradient in the convolution adjoint reached 2^16 (outside the fixed-point range)");
+    SN_CHECK(f[FLAG_EDGE_OVERFLOW] == 0, SEVENNET_EOVERFLOW, "neighbour list larger than its capacity");
+    SN_CHECK(f[2] == 0, SEVENNET_ECUDA, "internal error: reverse edge not found");
+    return SEVENNET_OK;
+}
+
+// Edge capacity for a batch of N atoms: 64 neighbours per atom (the densest
+// synthetic cells have about 50 within 5 A), grown to a larger count seen.
+void reserve_edges(sevennet_model* M, Workspace* ws, int64_t N, int64_t need, sevennet_status* s) {
+    const int64_t cap = std::max<int64_t>({ws->cap_edges, N * 64, need + need / 4 + 1024, 1024});
+    *s = ws_reserve(M, ws, std::max<int64_t>(N, ws->cap_atoms), cap, ws->cap_bins - 1, ws->cap_structs,
+                    nullptr);
+}
+
+// Evaluate a batch whose positions and species are already on the device: one
+// host synchronisation, at the end; an overflow of the edge capacity is retried
+// once with the count the device reported.
 sevennet_status eval_batch(sevennet_model* M, Workspace* ws, const BatchHost& b,
                            const int32_t* species_dev, const double* pos_dev, sevennet_precision prec,
                            double* energy_dev, double* forces_dev, double* virial_dev, cudaStream_t st) {
     SN_TRY(check_batch(b));
     SN_CHECK(prec == SEVENNET_FP32 || prec == SEVENNET_BF16, SEVENNET_EINVAL, "unknown precision");
     const int64_t N = b.atom_off[b.n_structs];
-    int64_t E = 0;
-    cudaEvent_t ev;
-    prof_begin(&M->prof, PF_NEIGHBORS, st, &ev);
-    SN_TRY(build_neighbors(M, ws, b, pos_dev, species_dev, st, &E));
-    prof_end(&M->prof, PF_NEIGHBORS, st, ev, 9);
-    count_launches(10);
-    if (N > 0) {
-        check_species_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, species_dev, M->cfg.n_species,
-                                                                          ws->flags);
+    int64_t need = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        sevennet_status rs;
+        reserve_edges(M, ws, N, need, &rs);
+        SN_TRY(rs);
+        SN_CUDA(cudaMemsetAsync(ws->flags, 0, FLAG_WORDS * sizeof(int), st));
+        SN_TRY(eval_enqueue(M, ws, b, species_dev, pos_dev, prec, energy_dev, forces_dev, virial_dev, st));
+        SN_CUDA(cudaMemcpyAsync(ws->flags_host, ws->flags, FLAG_WORDS * sizeof(int), cudaMemcpyDeviceToHost, st));
+        SN_CUDA(cudaStreamSynchronize(st));
+        if (ws->flags_host[FLAG_EDGE_OVERFLOW] && attempt == 0) {
+            need = ws->flags_host[FLAG_EDGE_NEED];
+            continue;
+        }
+        return check_flags(ws->flags_host);
     }
-    SN_TRY(run_model(M, ws, b, E, prec, energy_dev, forces_dev, virial_dev, st));
-    SN_CUDA(cudaMemcpyAsync(ws->flags_host, ws->flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    SN_CUDA(cudaStreamSynchronize(st));
-    SN_CHECK(ws->flags_host[3] == 0, SEVENNET_EINVAL, "species index out of range");
-    SN_CHECK(ws->flags_host[FLAG_GX_OVERFLOW] == 0, SEVENNET_EOVERFLOW,
-             "a feature gradient in the convolution adjoint reached 2^16 (outside the fixed-point range)");
-    SN_CHECK(ws->flags_host[2] == 0, SEVENNET_ECUDA, "internal error: reverse edge not found");
     return SEVENNET_OK;
 }
 

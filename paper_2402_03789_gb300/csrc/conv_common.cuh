@@ -603,10 +603,12 @@ __device__ __forceinline__ void chunk_w_gemm_f32(const ConvDesc& D, const ConvSm
     __syncthreads();
 }
 
-// Receiver range of this CTA, balanced by edges.
-__device__ __forceinline__ void cta_range(int n_atoms, int n_edges, const int* __restrict__ row_ptr,
+// Receiver range of this CTA, balanced by edges.  The edge count is taken from
+// row_ptr[n_atoms] (the host may not know it: asynchronous neighbour builds).
+__device__ __forceinline__ void cta_range(int n_atoms, int /*n_edges*/, const int* __restrict__ row_ptr,
                                           int* s_range) {
     if (threadIdx.x == 0) {
+        const int n_edges = row_ptr[n_atoms];
         const int nb = gridDim.x, b = blockIdx.x;
         auto lb = [&](long long key) {
             int lo = 0, hi = n_atoms;      // first v in [0, n_atoms] with row_ptr[v] >= key

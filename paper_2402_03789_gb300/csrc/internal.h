@@ -356,7 +356,7 @@ struct Workspace {
     double* e_atom = nullptr;     // [N]
     double* w_atom = nullptr;     // [N][9]
     double* f_s = nullptr;        // [N][3] forces, internal order
-    int* flags = nullptr;         // [8] device status words
+    int* flags = nullptr;         // [FLAG_WORDS] device status words
     int* flags_host = nullptr;    // pinned mirror
     std::vector<void*> allocs;
 };
@@ -377,14 +377,19 @@ struct BatchHost {
 // order.  Leaves ws->row_ptr/src/dst/shift/geom/rev and the internal order.
 // r_list > 0 builds the list for that cutoff instead of the model's r_c (the
 // Verlet list of MD with a skin).
+// async: no host synchronisation (the caller has reserved the edge capacity and
+// cleared the flags; *n_edges_out = -1 and the count stays on the device);
+// cond (device int, may be null): every kernel skips when *cond is 0.
 sevennet_status build_neighbors(sevennet_model* M, Workspace* ws, const BatchHost& b,
                                 const double* pos_dev, const int32_t* species_dev,
-                                cudaStream_t st, int64_t* n_edges_out, double r_list = 0.0);
+                                cudaStream_t st, int64_t* n_edges_out, double r_list = 0.0,
+                                const int* cond = nullptr, bool async = false);
 
 // The edges of a stored Verlet list (CSR in the internal order of the build that
 // made it: row_ptr, src, shift) that are within the model's r_c at the current
 // positions (input order), kept in list order, into ws->row_ptr/src/dst/shift/
 // geom/rev.  One structure; the internal order and cell of that build stay valid.
+// Asynchronous (*n_edges_out = -1; the count stays on the device).
 sevennet_status refresh_neighbors(sevennet_model* M, Workspace* ws, int64_t n_atoms, const double* pos_dev,
                                   const int* list_row_ptr, const int* list_src, const int* list_shift,
                                   cudaStream_t st, int64_t* n_edges_out);
@@ -404,6 +409,14 @@ sevennet_status model_layer_backward_rest(sevennet_model* M, Workspace* ws, int 
 sevennet_status run_model(sevennet_model* M, Workspace* ws, const BatchHost& b, int64_t n_edges,
                           sevennet_precision prec, double* energy_dev, double* forces_dev,
                           double* virial_dev, cudaStream_t st);
+
+// Device status words of a workspace: [0] edge count of the last build or
+// refresh, [1] two atoms closer than 1e-8 A, [2] reverse edge missing, [3]
+// species out of range, [FLAG_GX_OVERFLOW], [FLAG_EDGE_OVERFLOW] edges beyond
+// the capacity, [FLAG_EDGE_NEED] the largest edge count asked for, [7] spare.
+constexpr int FLAG_WORDS = 8;
+constexpr int FLAG_EDGE_OVERFLOW = 4;
+constexpr int FLAG_EDGE_NEED = 6;
 
 // Deterministic scatter of dE/dx in the convolution adjoint: every per-edge
 // contribution v is added as the 64-bit integer round(v * 2^36) (fixed point),
@@ -458,6 +471,11 @@ void conv_prepare_edges(int64_t n_atoms, int64_t n_edges, const int* row_ptr, co
                         int* dst, float4* geom, cudaStream_t st);
 
 // shared by the C ABI front ends (api.cu, md_server.cu)
+sevennet_status eval_enqueue(sevennet_model* M, Workspace* ws, const BatchHost& b,
+                             const int32_t* species_dev, const double* pos_dev, sevennet_precision prec,
+                             double* energy_dev, double* forces_dev, double* virial_dev, cudaStream_t st);
+sevennet_status check_flags(const int* flags_host);
+void reserve_edges(sevennet_model* M, Workspace* ws, int64_t N, int64_t need, sevennet_status* s);
 sevennet_status eval_batch(sevennet_model* M, Workspace* ws, const BatchHost& b,
                            const int32_t* species_dev, const double* pos_dev,
                            sevennet_precision prec, double* energy_dev, double* forces_dev,

@@ -110,6 +110,40 @@ __global__ void max_disp_kernel(int64_t n, const double* __restrict__ pos, const
     if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(d2));
 }
 
+// The rebuild decision of the Verlet list, on the device: cond = 1 when some
+// atom has moved more than half the skin since the list's build (or force is
+// set); the displacement maximum is cleared for the next step and the build
+// counter advanced.
+__global__ void rebuild_decision_kernel(unsigned long long* __restrict__ dmax, double thr2, int force,
+                                        int* __restrict__ cond, long long* __restrict__ builds) {
+    const double d2 = __longlong_as_double((long long)*dmax);
+    const int c = force || !(d2 <= thr2);
+    *cond = c;
+    *dmax = 0ull;
+    if (c) *builds += 1;
+}
+
+// Keep the freshly built list (cutoff r_c + skin) and the positions it was built
+// at, when cond is set: row_ptr [n + 1], src and shift [row_ptr[n]].
+__global__ void keep_list_kernel(int64_t n, int64_t cap, const int* __restrict__ cond,
+                                 const int* __restrict__ row_ptr, const int* __restrict__ src,
+                                 const int* __restrict__ shift, const double* __restrict__ pos,
+                                 int* __restrict__ l_row, int* __restrict__ l_src, int* __restrict__ l_shift,
+                                 double* __restrict__ ref) {
+    if (!*cond) return;
+    const int64_t total = row_ptr[n];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i <= n) l_row[i] = row_ptr[i];
+        if (i < 3 * n) ref[i] = pos[i];
+        if (i < total) {
+            l_src[i] = src[i];
+            l_shift[i * 3] = shift[i * 3];
+            l_shift[i * 3 + 1] = shift[i * 3 + 1];
+            l_shift[i * 3 + 2] = shift[i * 3 + 2];
+        }
+    }
+}
+
 }  // namespace sn
 
 using namespace sn;
@@ -131,8 +165,12 @@ struct sevennet_md {
     int64_t l_cap = 0;
     double* ref = nullptr;
     unsigned long long* dmax = nullptr;
-    unsigned long long* dmax_host = nullptr;
+    int* cond = nullptr;                 // device: rebuild the list this step
+    long long* builds = nullptr;         // device: list builds so far
     bool have_list = false;
+    // state at the start of the current md_step call (restored for a retry)
+    double *pos0 = nullptr, *vel0 = nullptr, *f0 = nullptr, *nh0 = nullptr;
+    long long* builds0 = nullptr;
     // Nose-Hoover thermostat (tau > 0): {xi, eta} on the device
     double nh_T0 = 0.0, nh_tau = 0.0;
     // linear ramp of the target from nh_T0 to nh_T1 over nh_ramp steps (0: none);
@@ -143,67 +181,58 @@ struct sevennet_md {
     int64_t n_builds = 0, n_edges = 0;
 };
 
-// Forces at the current positions.  Without a skin: a full neighbour build and
-// evaluation.  With a skin: the stored Verlet list (cutoff r_c + skin) is rebuilt
-// when some atom has moved more than skin / 2 since its build, and otherwise
-// filtered to r < r_c at the current positions (no pair can have entered r_c).
-static sevennet_status md_evaluate(sevennet_md* md) {
-    sevennet_model* M = md->M;
-    if (md->skin <= 0.0) {
-        SN_TRY(eval_batch(M, md->ws, md->b, md->species, md->pos, md->prec, md->ev, md->f, md->ev + 1, md->st));
-        ++md->n_builds;
-        return SEVENNET_OK;
-    }
-    bool rebuild = !md->have_list;
-    if (!rebuild) {
-        SN_CUDA(cudaMemsetAsync(md->dmax, 0, sizeof(unsigned long long), md->st));
-        max_disp_kernel<<<(unsigned)((md->N + 255) / 256), 256, 0, md->st>>>(md->N, md->pos, md->ref, md->dmax);
-        SN_CUDA(cudaMemcpyAsync(md->dmax_host, md->dmax, sizeof(unsigned long long), cudaMemcpyDeviceToHost, md->st));
-        SN_CUDA(cudaStreamSynchronize(md->st));
-        double d2;
-        std::memcpy(&d2, md->dmax_host, sizeof(double));
-        rebuild = !(d2 <= 0.25 * md->skin * md->skin);
-    }
-    const int64_t N = md->N;
-    if (rebuild) {
-        int64_t EL = 0;
-        SN_TRY(build_neighbors(M, md->ws, md->b, md->pos, md->species, md->st, &EL, M->cfg.r_cut + md->skin));
-        if (EL > md->l_cap) {
-            cudaFree(md->l_src);
-            cudaFree(md->l_shift);
-            md->l_src = md->l_shift = nullptr;
-            md->l_cap = 0;
-            const int64_t cap = EL + EL / 4 + 1024;
-            if (cudaMalloc(&md->l_src, cap * sizeof(int)) || cudaMalloc(&md->l_shift, cap * 3 * sizeof(int))) {
-                cudaGetLastError();
-                set_error("cudaMalloc failed for the Verlet list");
-                return SEVENNET_ENOMEM;
-            }
-            md->l_cap = cap;
-        }
-        if (!md->l_row && cudaMalloc(&md->l_row, (N + 1) * sizeof(int))) {
+// Room for the edge lists of this MD run: the evaluation's own list and, with
+// a skin, the Verlet list (cutoff r_c + skin), each at least `need` edges.
+static sevennet_status md_reserve(sevennet_md* md, int64_t need) {
+    sevennet_status s;
+    reserve_edges(md->M, md->ws, md->N, need, &s);
+    SN_TRY(s);
+    const int64_t cap = md->ws->cap_edges;
+    if (md->skin > 0.0 && cap > md->l_cap) {
+        cudaFree(md->l_src);
+        cudaFree(md->l_shift);
+        md->l_src = md->l_shift = nullptr;
+        md->l_cap = 0;
+        if (cudaMalloc(&md->l_src, cap * sizeof(int)) || cudaMalloc(&md->l_shift, cap * 3 * sizeof(int))) {
             cudaGetLastError();
             set_error("cudaMalloc failed for the Verlet list");
             return SEVENNET_ENOMEM;
         }
-        SN_CUDA(cudaMemcpyAsync(md->l_row, md->ws->row_ptr, (N + 1) * sizeof(int), cudaMemcpyDeviceToDevice, md->st));
-        if (EL > 0) {
-            SN_CUDA(cudaMemcpyAsync(md->l_src, md->ws->src, EL * sizeof(int), cudaMemcpyDeviceToDevice, md->st));
-            SN_CUDA(cudaMemcpyAsync(md->l_shift, md->ws->shift, EL * 3 * sizeof(int), cudaMemcpyDeviceToDevice,
-                                    md->st));
-        }
-        SN_CUDA(cudaMemcpyAsync(md->ref, md->pos, N * 3 * sizeof(double), cudaMemcpyDeviceToDevice, md->st));
-        md->have_list = true;
-        ++md->n_builds;
+        md->l_cap = cap;
     }
-    int64_t E = 0;
-    SN_TRY(refresh_neighbors(M, md->ws, N, md->pos, md->l_row, md->l_src, md->l_shift, md->st, &E));
-    md->n_edges = E;
-    SN_TRY(run_model(M, md->ws, md->b, E, md->prec, md->ev, md->f, md->ev + 1, md->st));
-    SN_CUDA(cudaMemcpyAsync(md->ws->flags_host, md->ws->flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, md->st));
-    SN_CUDA(cudaStreamSynchronize(md->st));
-    SN_CHECK(md->ws->flags_host[2] == 0, SEVENNET_ECUDA, "internal error: reverse edge not found");
+    if (md->skin > 0.0 && !md->l_row && cudaMalloc(&md->l_row, (md->N + 1) * sizeof(int))) {
+        cudaGetLastError();
+        set_error("cudaMalloc failed for the Verlet list");
+        return SEVENNET_ENOMEM;
+    }
     return SEVENNET_OK;
+}
+
+// Forces at the current positions, enqueued without a host synchronisation.
+// Without a skin: a full neighbour build and evaluation.  With a skin: the
+// stored Verlet list (cutoff r_c + skin) is rebuilt when some atom has moved
+// more than skin / 2 since its build (decided on the device), and otherwise
+// filtered to r < r_c at the current positions (no pair can have entered r_c).
+static sevennet_status md_evaluate(sevennet_md* md) {
+    sevennet_model* M = md->M;
+    if (md->skin <= 0.0) {
+        SN_TRY(eval_enqueue(M, md->ws, md->b, md->species, md->pos, md->prec, md->ev, md->f, md->ev + 1, md->st));
+        ++md->n_builds;
+        return SEVENNET_OK;
+    }
+    const int64_t N = md->N;
+    max_disp_kernel<<<(unsigned)((N + 255) / 256), 256, 0, md->st>>>(N, md->pos, md->ref, md->dmax);
+    rebuild_decision_kernel<<<1, 1, 0, md->st>>>(md->dmax, 0.25 * md->skin * md->skin, md->have_list ? 0 : 1,
+                                                 md->cond, md->builds);
+    int64_t E = -1;
+    SN_TRY(build_neighbors(M, md->ws, md->b, md->pos, md->species, md->st, &E, M->cfg.r_cut + md->skin,
+                           md->cond, true));
+    keep_list_kernel<<<(unsigned)std::min<int64_t>((md->l_cap + 255) / 256 + 1, 4096), 256, 0, md->st>>>(
+        N, std::max<int64_t>(md->l_cap, 3 * N + 1), md->cond, md->ws->row_ptr, md->ws->src, md->ws->shift, md->pos,
+        md->l_row, md->l_src, md->l_shift, md->ref);
+    md->have_list = true;
+    SN_TRY(refresh_neighbors(M, md->ws, N, md->pos, md->l_row, md->l_src, md->l_shift, md->st, &E));
+    return run_model(M, md->ws, md->b, -1, md->prec, md->ev, md->f, md->ev + 1, md->st);
 }
 
 extern "C" {
@@ -226,7 +255,13 @@ void sevennet_md_destroy(sevennet_md* md) {
     cudaFree(md->ref);
     cudaFree(md->dmax);
     cudaFree(md->nh);
-    if (md->dmax_host) cudaFreeHost(md->dmax_host);
+    cudaFree(md->cond);
+    cudaFree(md->builds);
+    cudaFree(md->pos0);
+    cudaFree(md->vel0);
+    cudaFree(md->f0);
+    cudaFree(md->nh0);
+    cudaFree(md->builds0);
     ws_free(md->ws);
     if (md->st) cudaStreamDestroy(md->st);
     delete md;
@@ -263,7 +298,9 @@ sevennet_status sevennet_md_create(sevennet_model* M, int64_t n_atoms, const int
         cudaMalloc(&md->vel, n3) || cudaMalloc(&md->f, n3) || cudaMalloc(&md->inv_m, n_atoms * sizeof(double)) ||
         cudaMalloc(&md->ev, 16 * sizeof(double)) || cudaMalloc(&md->ref, n3) ||
         cudaMalloc(&md->dmax, sizeof(unsigned long long)) || cudaMalloc(&md->nh, 2 * sizeof(double)) ||
-        cudaMallocHost(&md->dmax_host, sizeof(unsigned long long))) {
+        cudaMalloc(&md->cond, sizeof(int)) || cudaMalloc(&md->builds, sizeof(long long)) ||
+        cudaMalloc(&md->pos0, n3) || cudaMalloc(&md->vel0, n3) || cudaMalloc(&md->f0, n3) ||
+        cudaMalloc(&md->nh0, 2 * sizeof(double)) || cudaMalloc(&md->builds0, sizeof(long long))) {
         cudaGetLastError();
         set_error("cudaMalloc failed for MD state");
         return fail(SEVENNET_ENOMEM);
@@ -274,14 +311,76 @@ sevennet_status sevennet_md_create(sevennet_model* M, int64_t n_atoms, const int
         set_error("copy of MD state failed");
         return fail(SEVENNET_ECUDA);
     }
-    if (cudaMemset(md->nh, 0, 2 * sizeof(double))) {
+    if (cudaMemset(md->nh, 0, 2 * sizeof(double)) || cudaMemset(md->dmax, 0, sizeof(unsigned long long)) ||
+        cudaMemset(md->builds, 0, sizeof(long long))) {
         set_error("cudaMemset failed");
         return fail(SEVENNET_ECUDA);
     }
     sevennet_status s = eval_batch(M, md->ws, md->b, md->species, md->pos, prec, md->ev, md->f, md->ev + 1, md->st);
     if (s) return fail(s);
     md->n_builds = 1;
+    md->n_edges = md->ws->flags_host[0];
     *out = md;
+    return SEVENNET_OK;
+}
+
+// One call runs n_steps steps without a host synchronisation (the neighbour
+// lists keep their edge counts on the device) and synchronises once at the end.
+// An edge list that outgrew its capacity is reported by the device; the call
+// then restores the state it started from, enlarges the capacity and runs again.
+static sevennet_status md_run(sevennet_md* md, int64_t n_steps, double dt_fs, bool retry) {
+    const int64_t n3 = md->N * 3;
+    const unsigned blocks = (unsigned)((n3 + 255) / 256);
+    const bool nvt = md->nh_tau > 0.0;
+    const size_t b3 = (size_t)n3 * sizeof(double);
+    SN_CUDA(cudaMemcpyAsync(md->pos0, md->pos, b3, cudaMemcpyDeviceToDevice, md->st));
+    SN_CUDA(cudaMemcpyAsync(md->vel0, md->vel, b3, cudaMemcpyDeviceToDevice, md->st));
+    SN_CUDA(cudaMemcpyAsync(md->f0, md->f, b3, cudaMemcpyDeviceToDevice, md->st));
+    SN_CUDA(cudaMemcpyAsync(md->nh0, md->nh, 2 * sizeof(double), cudaMemcpyDeviceToDevice, md->st));
+    SN_CUDA(cudaMemcpyAsync(md->builds0, md->builds, sizeof(long long), cudaMemcpyDeviceToDevice, md->st));
+    const int64_t nh_done0 = md->nh_done, builds0 = md->n_builds;
+    SN_CUDA(cudaMemsetAsync(md->ws->flags, 0, FLAG_WORDS * sizeof(int), md->st));
+    for (int64_t k = 0; k < n_steps; ++k) {
+        // target of this step: the ramp's value at the middle of the step, then its end value
+        double t0 = md->nh_T0;
+        if (md->nh_ramp > 0) {
+            const double x = std::min((double)md->nh_done + 0.5, (double)md->nh_ramp) / (double)md->nh_ramp;
+            t0 = md->nh_T0 + (md->nh_T1 - md->nh_T0) * x;
+            if (md->nh_done < md->nh_ramp) ++md->nh_done;
+        }
+        const double nf_kt0 = (3.0 * md->N - 3.0) * KB_EV * t0;
+        const double q = nf_kt0 * md->nh_tau * md->nh_tau;
+        if (nvt) nh_half_kernel<<<1, 1024, 0, md->st>>>(md->N, 0.5 * dt_fs, md->inv_m, md->vel, md->nh, nf_kt0, q);
+        kick_drift_kernel<<<blocks, 256, 0, md->st>>>(md->N, dt_fs, md->inv_m, md->f, md->vel, md->pos);
+        SN_TRY(md_evaluate(md));
+        kick_kernel<<<blocks, 256, 0, md->st>>>(md->N, dt_fs, md->inv_m, md->f, md->vel);
+        if (nvt) nh_half_kernel<<<1, 1024, 0, md->st>>>(md->N, 0.5 * dt_fs, md->inv_m, md->vel, md->nh, nf_kt0, q);
+        energies_kernel<<<1, 1024, 0, md->st>>>(md->N, md->inv_m, md->vel, md->ev, md->ekin + k, md->epot + k);
+    }
+    SN_CUDA(cudaGetLastError());
+    long long builds = 0;
+    SN_CUDA(cudaMemcpyAsync(md->ws->flags_host, md->ws->flags, FLAG_WORDS * sizeof(int), cudaMemcpyDeviceToHost,
+                            md->st));
+    SN_CUDA(cudaMemcpyAsync(&builds, md->builds, sizeof(long long), cudaMemcpyDeviceToHost, md->st));
+    SN_CUDA(cudaStreamSynchronize(md->st));
+    const int* fl = md->ws->flags_host;
+    if (fl[FLAG_EDGE_OVERFLOW] && retry) {
+        const int64_t need = fl[FLAG_EDGE_NEED];
+        SN_CUDA(cudaMemcpyAsync(md->pos, md->pos0, b3, cudaMemcpyDeviceToDevice, md->st));
+        SN_CUDA(cudaMemcpyAsync(md->vel, md->vel0, b3, cudaMemcpyDeviceToDevice, md->st));
+        SN_CUDA(cudaMemcpyAsync(md->f, md->f0, b3, cudaMemcpyDeviceToDevice, md->st));
+        SN_CUDA(cudaMemcpyAsync(md->nh, md->nh0, 2 * sizeof(double), cudaMemcpyDeviceToDevice, md->st));
+        SN_CUDA(cudaMemcpyAsync(md->builds, md->builds0, sizeof(long long), cudaMemcpyDeviceToDevice, md->st));
+        SN_CUDA(cudaStreamSynchronize(md->st));
+        md->have_list = false;                      // the list arrays are reallocated
+        md->nh_done = nh_done0;
+        md->n_builds = builds0;
+        SN_TRY(md_reserve(md, need));
+        return md_run(md, n_steps, dt_fs, false);
+    }
+    SN_TRY(check_flags(fl));
+    if (md->skin > 0.0) md->n_builds = 1 + builds;
+    md->n_edges = fl[0];
     return SEVENNET_OK;
 }
 
@@ -301,32 +400,14 @@ sevennet_status sevennet_md_step(sevennet_md* md, int64_t n_steps, double dt_fs,
         }
         md->log_cap = n_steps;
     }
-    const int64_t n3 = md->N * 3;
-    const unsigned blocks = (unsigned)((n3 + 255) / 256);
-    const bool nvt = md->nh_tau > 0.0;
-    for (int64_t k = 0; k < n_steps; ++k) {
-        // target of this step: the ramp's value at the middle of the step, then its end value
-        double t0 = md->nh_T0;
-        if (md->nh_ramp > 0) {
-            const double x = std::min((double)md->nh_done + 0.5, (double)md->nh_ramp) / (double)md->nh_ramp;
-            t0 = md->nh_T0 + (md->nh_T1 - md->nh_T0) * x;
-            if (md->nh_done < md->nh_ramp) ++md->nh_done;
-        }
-        const double nf_kt0 = (3.0 * md->N - 3.0) * KB_EV * t0;
-        const double q = nf_kt0 * md->nh_tau * md->nh_tau;
-        if (nvt) nh_half_kernel<<<1, 1024, 0, md->st>>>(md->N, 0.5 * dt_fs, md->inv_m, md->vel, md->nh, nf_kt0, q);
-        kick_drift_kernel<<<blocks, 256, 0, md->st>>>(md->N, dt_fs, md->inv_m, md->f, md->vel, md->pos);
-        SN_TRY(md_evaluate(md));
-        kick_kernel<<<blocks, 256, 0, md->st>>>(md->N, dt_fs, md->inv_m, md->f, md->vel);
-        if (nvt) nh_half_kernel<<<1, 1024, 0, md->st>>>(md->N, 0.5 * dt_fs, md->inv_m, md->vel, md->nh, nf_kt0, q);
-        energies_kernel<<<1, 1024, 0, md->st>>>(md->N, md->inv_m, md->vel, md->ev, md->ekin + k, md->epot + k);
-    }
-    SN_CUDA(cudaGetLastError());
-    if (n_steps > 0) {
-        if (epot_log) SN_CUDA(cudaMemcpyAsync(epot_log, md->epot, n_steps * sizeof(double), cudaMemcpyDeviceToHost, md->st));
-        if (ekin_log) SN_CUDA(cudaMemcpyAsync(ekin_log, md->ekin, n_steps * sizeof(double), cudaMemcpyDeviceToHost, md->st));
-    }
-    SN_CUDA(cudaStreamSynchronize(md->st));
+    if (n_steps == 0) return SEVENNET_OK;
+    // edge capacity: the first evaluation's count with room for density
+    // fluctuations and, with a skin, for the longer Verlet list
+    const double grow = md->skin > 0.0 ? std::pow((md->M->cfg.r_cut + md->skin) / md->M->cfg.r_cut, 3.0) : 1.0;
+    SN_TRY(md_reserve(md, (int64_t)(1.2 * grow * (double)std::max<int64_t>(md->n_edges, 0))));
+    SN_TRY(md_run(md, n_steps, dt_fs, true));
+    if (epot_log) SN_CUDA(cudaMemcpy(epot_log, md->epot, n_steps * sizeof(double), cudaMemcpyDeviceToHost));
+    if (ekin_log) SN_CUDA(cudaMemcpy(ekin_log, md->ekin, n_steps * sizeof(double), cudaMemcpyDeviceToHost));
     return SEVENNET_OK;
 }
 
@@ -423,6 +504,8 @@ struct SrvSlot {
     bool busy = false;
     std::vector<SrvReq> reqs;
     std::vector<int64_t> off;
+    BatchHost batch;
+    int* h_flags = nullptr;
     size_t bytes = 0;
     int32_t batch_id = -1;
     double start_s = 0;
@@ -451,6 +534,7 @@ struct sevennet_server {
     bool stop = false;
     uint64_t next_ticket = 1;
     int32_t next_batch = 0;
+    int64_t slot_atoms = 0;              // atoms one slot (one batch) can hold
     std::chrono::steady_clock::time_point t0;
 };
 
@@ -460,46 +544,43 @@ static double srv_now(const sevennet_server* s) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
 }
 
-// Predicted device bytes of one request: activations per atom plus per-edge
-// arrays at a generous 80 neighbours per atom.
-static size_t predict_bytes(const sevennet_model* M, int64_t n) {
-    const size_t per_atom = (size_t)(M->T * (M->x_max + M->y_max) + M->m_max + M->y_max + M->x_max +
-                                     2 * M->h_max) * sizeof(float) + 200;
+// Device bytes per atom of a slot's workspace: the activations of every block,
+// the messages and gradients, the fixed-point dE/dx sums, and 64 edges.
+static size_t bytes_per_atom(const sevennet_model* M) {
+    const size_t act = (size_t)(M->T * (M->x_max + M->y_max) + M->m_max + M->y_max + M->x_max + 2 * M->h_max) *
+                           sizeof(float) + (size_t)M->x_max * sizeof(unsigned long long) + 200;
     const size_t per_edge = 4 * 4 + 12 + 16 + 12;
-    return per_atom * (size_t)n + per_edge * (size_t)n * 80 + 4096;
+    return act + per_edge * 64;
 }
 
-static sevennet_status slot_reserve(SrvSlot& sl, int64_t atoms, int32_t structs) {
-    if (atoms > sl.cap_atoms) {
-        cudaFree(sl.pos); cudaFree(sl.forces); cudaFree(sl.species);
-        cudaFreeHost(sl.h_pos); cudaFreeHost(sl.h_forces); cudaFreeHost(sl.h_species);
-        const int64_t A = std::max<int64_t>(atoms * 5 / 4, 256);
-        if (cudaMalloc(&sl.pos, A * 3 * sizeof(double)) || cudaMalloc(&sl.forces, A * 3 * sizeof(double)) ||
-            cudaMalloc(&sl.species, A * sizeof(int32_t)) || cudaMallocHost(&sl.h_pos, A * 3 * sizeof(double)) ||
-            cudaMallocHost(&sl.h_forces, A * 3 * sizeof(double)) || cudaMallocHost(&sl.h_species, A * sizeof(int32_t))) {
-            cudaGetLastError();
-            sl.cap_atoms = 0;
-            set_error("server: allocation failed");
-            return SEVENNET_ENOMEM;
-        }
-        sl.cap_atoms = A;
+// Predicted device bytes of one request (its share of a slot's workspace).
+static size_t predict_bytes(const sevennet_model* M, int64_t n) { return bytes_per_atom(M) * (size_t)n + 4096; }
+
+// A slot's workspace and pinned buffers are allocated once, at server creation,
+// for cap_atoms atoms (its share of the HBM budget), so that running a batch
+// neither allocates nor frees (either would wait for the whole device).
+static sevennet_status slot_alloc(sevennet_model* M, SrvSlot& sl, int64_t atoms, int32_t structs) {
+    const int64_t A = std::max<int64_t>(atoms, 1);
+    if (cudaMalloc(&sl.pos, A * 3 * sizeof(double)) || cudaMalloc(&sl.forces, A * 3 * sizeof(double)) ||
+        cudaMalloc(&sl.species, A * sizeof(int32_t)) || cudaMallocHost(&sl.h_pos, A * 3 * sizeof(double)) ||
+        cudaMallocHost(&sl.h_forces, A * 3 * sizeof(double)) || cudaMallocHost(&sl.h_species, A * sizeof(int32_t)) ||
+        cudaMalloc(&sl.energy, structs * sizeof(double)) || cudaMalloc(&sl.virial, structs * 9 * sizeof(double)) ||
+        cudaMallocHost(&sl.h_energy, structs * sizeof(double)) ||
+        cudaMallocHost(&sl.h_virial, structs * 9 * sizeof(double)) ||
+        cudaMallocHost(&sl.h_flags, FLAG_WORDS * sizeof(int))) {
+        cudaGetLastError();
+        set_error("server: allocation of %lld atoms per slot failed", (long long)A);
+        return SEVENNET_ENOMEM;
     }
-    if (structs > sl.cap_structs) {
-        cudaFree(sl.energy); cudaFree(sl.virial); cudaFreeHost(sl.h_energy); cudaFreeHost(sl.h_virial);
-        const int32_t S = std::max<int32_t>(structs, 64);
-        if (cudaMalloc(&sl.energy, S * sizeof(double)) || cudaMalloc(&sl.virial, S * 9 * sizeof(double)) ||
-            cudaMallocHost(&sl.h_energy, S * sizeof(double)) || cudaMallocHost(&sl.h_virial, S * 9 * sizeof(double))) {
-            cudaGetLastError();
-            sl.cap_structs = 0;
-            set_error("server: allocation failed");
-            return SEVENNET_ENOMEM;
-        }
-        sl.cap_structs = S;
-    }
-    return SEVENNET_OK;
+    sl.cap_atoms = A;
+    sl.cap_structs = structs;
+    // workspace: atoms, 64 edges per atom, cell-list bins and structure descriptors
+    return ws_reserve(M, sl.ws, A, std::max<int64_t>(A * 64, 1024), A + 128 * (int64_t)structs, structs, sl.st);
 }
 
-// Enqueue one packed batch on a slot (returns after the neighbour count read).
+// Enqueue one packed batch on a slot: copies, neighbour build and evaluation with
+// the edge count kept on the device, results and status words back into pinned
+// memory, an event at the end.  No host synchronisation, no allocation.
 static sevennet_status slot_launch(sevennet_server* S, SrvSlot& sl) {
     const int32_t ns = (int32_t)sl.reqs.size();
     sl.start_s = srv_now(S);
@@ -513,26 +594,44 @@ static sevennet_status slot_launch(sevennet_server* S, SrvSlot& sl) {
         std::copy(sl.reqs[i].cell, sl.reqs[i].cell + 9, &b.cells[(size_t)i * 9]);
     }
     const int64_t N = b.atom_off[ns];
-    SN_TRY(slot_reserve(sl, N, ns));
+    SN_CHECK(N <= sl.cap_atoms && ns <= sl.cap_structs, SEVENNET_ECUDA, "internal error: batch exceeds its slot");
     for (int32_t i = 0; i < ns; ++i) {
         std::copy(sl.reqs[i].pos.begin(), sl.reqs[i].pos.end(), sl.h_pos + b.atom_off[i] * 3);
         std::copy(sl.reqs[i].species.begin(), sl.reqs[i].species.end(), sl.h_species + b.atom_off[i]);
     }
+    SN_TRY(check_batch(b));
     SN_CUDA(cudaMemcpyAsync(sl.pos, sl.h_pos, N * 3 * sizeof(double), cudaMemcpyHostToDevice, sl.st));
     SN_CUDA(cudaMemcpyAsync(sl.species, sl.h_species, N * sizeof(int32_t), cudaMemcpyHostToDevice, sl.st));
-    int64_t E = 0;
-    SN_TRY(check_batch(b));
-    SN_TRY(build_neighbors(S->M, sl.ws, b, sl.pos, sl.species, sl.st, &E));
-    SN_TRY(run_model(S->M, sl.ws, b, E, S->prec, sl.energy, sl.forces, sl.virial, sl.st));
+    SN_CUDA(cudaMemsetAsync(sl.ws->flags, 0, FLAG_WORDS * sizeof(int), sl.st));
+    SN_TRY(eval_enqueue(S->M, sl.ws, b, sl.species, sl.pos, S->prec, sl.energy, sl.forces, sl.virial, sl.st));
     SN_CUDA(cudaMemcpyAsync(sl.h_energy, sl.energy, ns * sizeof(double), cudaMemcpyDeviceToHost, sl.st));
     SN_CUDA(cudaMemcpyAsync(sl.h_virial, sl.virial, ns * 9 * sizeof(double), cudaMemcpyDeviceToHost, sl.st));
     SN_CUDA(cudaMemcpyAsync(sl.h_forces, sl.forces, N * 3 * sizeof(double), cudaMemcpyDeviceToHost, sl.st));
+    SN_CUDA(cudaMemcpyAsync(sl.h_flags, sl.ws->flags, FLAG_WORDS * sizeof(int), cudaMemcpyDeviceToHost, sl.st));
     SN_CUDA(cudaEventRecord(sl.ev, sl.st));
     sl.off = b.atom_off;
+    sl.batch = std::move(b);
+    return SEVENNET_OK;
+}
+
+// A batch whose edge list outgrew the slot's capacity runs again, synchronously,
+// through eval_batch (which enlarges the workspace); rare by construction.
+static sevennet_status slot_rerun(sevennet_server* S, SrvSlot& sl) {
+    const int32_t ns = sl.batch.n_structs;
+    const int64_t N = sl.batch.atom_off[ns];
+    SN_TRY(eval_batch(S->M, sl.ws, sl.batch, sl.species, sl.pos, S->prec, sl.energy, sl.forces, sl.virial, sl.st));
+    SN_CUDA(cudaMemcpyAsync(sl.h_energy, sl.energy, ns * sizeof(double), cudaMemcpyDeviceToHost, sl.st));
+    SN_CUDA(cudaMemcpyAsync(sl.h_virial, sl.virial, ns * 9 * sizeof(double), cudaMemcpyDeviceToHost, sl.st));
+    SN_CUDA(cudaMemcpyAsync(sl.h_forces, sl.forces, N * 3 * sizeof(double), cudaMemcpyDeviceToHost, sl.st));
+    SN_CUDA(cudaStreamSynchronize(sl.st));
     return SEVENNET_OK;
 }
 
 static void slot_finish(sevennet_server* S, SrvSlot& sl, sevennet_status status) {
+    if (status == SEVENNET_OK) {
+        if (sl.h_flags[FLAG_EDGE_OVERFLOW]) status = slot_rerun(S, sl);
+        else status = check_flags(sl.h_flags);
+    }
     const double now = srv_now(S);
     std::lock_guard<std::mutex> lk(S->mu);
     for (size_t i = 0; i < sl.reqs.size(); ++i) {
@@ -574,9 +673,11 @@ static void server_loop(sevennet_server* S) {
             std::unique_lock<std::mutex> lk(S->mu);
             if (S->stop && S->queue.empty()) break;
             size_t bytes = 0;
+            int64_t atoms = 0;
             while (!S->queue.empty() && (int32_t)free_slot->reqs.size() < S->max_structs &&
-                   S->in_flight + bytes + S->queue.front().bytes <= S->budget) {
+                   atoms + S->queue.front().n <= free_slot->cap_atoms) {
                 bytes += S->queue.front().bytes;
+                atoms += S->queue.front().n;
                 free_slot->reqs.push_back(std::move(S->queue.front()));
                 S->queue.pop_front();
             }
@@ -619,6 +720,7 @@ sevennet_status sevennet_server_create(sevennet_model* M, size_t hbm_budget_byte
                                        int32_t max_batch_structs, sevennet_precision prec, sevennet_server** out) {
     SN_CHECK(M && out && n_streams >= 1 && n_streams <= 16 && max_batch_structs >= 1 && hbm_budget_bytes > 0,
              SEVENNET_EINVAL, "bad argument");
+    SN_CHECK(prec == SEVENNET_FP32 || prec == SEVENNET_BF16, SEVENNET_EINVAL, "unknown precision");
     *out = nullptr;
     SN_ENTER(M->device);
     auto* S = new sevennet_server();
@@ -637,6 +739,15 @@ sevennet_status sevennet_server_create(sevennet_model* M, size_t hbm_budget_byte
             return SEVENNET_ECUDA;
         }
         sl.ws = new Workspace();
+    }
+    // each slot owns an equal share of the budget, allocated now
+    S->slot_atoms = (int64_t)((hbm_budget_bytes / (size_t)n_streams) / bytes_per_atom(M));
+    for (auto& sl : S->slots) {
+        const sevennet_status s = slot_alloc(M, sl, S->slot_atoms, max_batch_structs);
+        if (s != SEVENNET_OK) {
+            sevennet_server_destroy(S);
+            return s;
+        }
     }
     S->worker = std::thread(server_loop, S);
     *out = S;
@@ -657,8 +768,9 @@ sevennet_status sevennet_server_submit(sevennet_server* S, const sevennet_reques
     r.pos.assign(req->pos, req->pos + 3 * req->n_atoms);
     std::copy(req->cell, req->cell + 9, r.cell);
     r.bytes = predict_bytes(S->M, r.n);
-    SN_CHECK(r.bytes <= S->budget, SEVENNET_ENOMEM_ADMIT, "request needs %zu bytes, budget is %zu", r.bytes,
-             S->budget);
+    SN_CHECK(r.n <= S->slot_atoms, SEVENNET_ENOMEM_ADMIT,
+             "request of %lld atoms needs %zu bytes; a slot holds %lld atoms (its share of the %zu-byte budget)",
+             (long long)r.n, r.bytes, (long long)S->slot_atoms, S->budget);
     r.submit_s = srv_now(S);
     {
         std::lock_guard<std::mutex> lk(S->mu);
@@ -714,7 +826,7 @@ void sevennet_server_destroy(sevennet_server* S) {
         if (sl.st) cudaStreamSynchronize(sl.st);
         cudaFree(sl.pos); cudaFree(sl.forces); cudaFree(sl.species); cudaFree(sl.energy); cudaFree(sl.virial);
         cudaFreeHost(sl.h_pos); cudaFreeHost(sl.h_forces); cudaFreeHost(sl.h_species);
-        cudaFreeHost(sl.h_energy); cudaFreeHost(sl.h_virial);
+        cudaFreeHost(sl.h_energy); cudaFreeHost(sl.h_virial); cudaFreeHost(sl.h_flags);
         ws_free(sl.ws);
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.st) cudaStreamDestroy(sl.st);

@@ -1,7 +1,9 @@
 // Cell-list neighbour build for a batch of periodic cells (paper Sec. 2: an
 // edge joins v and w when |r_w - r_v| < r_c; every periodic image counts).
 //
-// Steps (all on the device, one host read of the edge count):
+// Steps (all on the device; the synchronous form reads the edge count back once,
+// the asynchronous form keeps it on the device and relies on a preallocated
+// capacity, with an overflow flag and a clamped CSR when that is too small):
 //   1. fractional coordinates, wrap along periodic directions, bin index
 //      (bins at least r_c wide per lattice direction, per structure);
 //   2. counting sort of atoms by bin, ties broken by input index, which fixes
@@ -28,12 +30,16 @@ __device__ __forceinline__ int struct_of_atom(const int64_t* __restrict__ atom_o
     return lo;
 }
 
+// cond (may be null): every kernel of the build returns at once when *cond is 0
+// (the Verlet-list rebuild of MD decided on the device).
+__device__ __forceinline__ bool skip(const int* cond) { return cond && *cond == 0; }
+
 __global__ void bin_atoms_kernel(int64_t n, int S, const int64_t* __restrict__ atom_off,
                                  const int* __restrict__ sdesc, const double* __restrict__ inv_cells,
                                  const double* __restrict__ pos, int* __restrict__ bin_of,
-                                 int* __restrict__ bin_count) {
+                                 int* __restrict__ bin_count, const int* cond) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || skip(cond)) return;
     const int s = struct_of_atom(atom_off, S, i);
     const int* d = sdesc + s * SD;
     const double* ic = inv_cells + s * 9;
@@ -55,7 +61,9 @@ __global__ void bin_atoms_kernel(int64_t n, int S, const int64_t* __restrict__ a
 
 // Exclusive scan of n ints into out[0..n] (out[n] = total) with one CTA.
 __global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ in, int64_t n,
-                                                    int* __restrict__ out, int* __restrict__ total) {
+                                                    int* __restrict__ out, int* __restrict__ total,
+                                                    const int* cond) {
+    if (skip(cond)) return;
     __shared__ int warp_sums[32];
     __shared__ int carry;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -95,18 +103,19 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ in, 
 }
 
 __global__ void place_kernel(int64_t n, const int* __restrict__ bin_of, const int* __restrict__ bin_start,
-                             int* __restrict__ bin_fill, int* __restrict__ perm) {
+                             int* __restrict__ bin_fill, int* __restrict__ perm, const int* cond) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || skip(cond)) return;
     const int b = bin_of[i];
     const int slot = atomicAdd(bin_fill + b, 1);
     perm[bin_start[b] + slot] = (int)i;
 }
 
 // Sort each bin's members by input index (deterministic internal order).
-__global__ void sort_bins_kernel(int64_t n_bins, const int* __restrict__ bin_start, int* __restrict__ perm) {
+__global__ void sort_bins_kernel(int64_t n_bins, const int* __restrict__ bin_start, int* __restrict__ perm,
+                                 const int* cond) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n_bins) return;
+    if (b >= n_bins || skip(cond)) return;
     const int s0 = bin_start[b], s1 = bin_start[b + 1];
     for (int i = s0 + 1; i < s1; ++i) {
         const int key = perm[i];
@@ -127,9 +136,9 @@ __global__ void gather_kernel(int64_t n, int S, const int64_t* __restrict__ atom
                               const double* __restrict__ inv_cells, const int* __restrict__ perm,
                               const double* __restrict__ pos, const int32_t* __restrict__ species,
                               double* __restrict__ pos_s, double* __restrict__ fl_s, float4* __restrict__ q32,
-                              int* __restrict__ species_s, int* __restrict__ struct_of) {
+                              int* __restrict__ species_s, int* __restrict__ struct_of, const int* cond) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || skip(cond)) return;
     const int64_t o = perm[i];
     const int s = struct_of_atom(atom_off, S, i);
     const int* d = sdesc + s * SD;
@@ -175,9 +184,9 @@ edges_kernel(int64_t n, double rc2, float rc32, int64_t cap, const int* __restri
              const double* __restrict__ q_s, const float4* __restrict__ q32, const double* __restrict__ fl_s,
              const int* __restrict__ row_ptr,
              int* __restrict__ counts, int* __restrict__ flags, int* __restrict__ dst, int* __restrict__ src,
-             int* __restrict__ shift, float4* __restrict__ geom) {
+             int* __restrict__ shift, float4* __restrict__ geom, const int* cond) {
     const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / NGL;
-    if (v >= n) return;                                    // the whole group leaves together
+    if (v >= n || skip(cond)) return;                      // the whole group leaves together
     const int j = threadIdx.x & (NGL - 1);
     const int gsh = threadIdx.x & 31 & ~(NGL - 1);
     const unsigned gmask = ((1u << NGL) - 1) << gsh;
@@ -274,11 +283,29 @@ edges_kernel(int64_t n, double rc2, float rc32, int64_t cap, const int* __restri
     }
 }
 
-__global__ void reverse_kernel(int64_t n_edges, const int* __restrict__ row_ptr, const int* __restrict__ dst,
+// Edge count over capacity: flags[0] holds the count the scan wrote.  When it
+// exceeds cap, row_ptr is clamped to cap (so that no later kernel reads past
+// the edge arrays), flags[FLAG_EDGE_OVERFLOW] is set and flags[FLAG_EDGE_NEED]
+// keeps the largest count seen, for the caller's retry with more room.
+__global__ void clamp_rows_kernel(int64_t n, int* __restrict__ row_ptr, int64_t cap, int* __restrict__ flags,
+                                  const int* cond) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n || skip(cond)) return;
+    const int total = flags[0];
+    if ((int64_t)total <= cap) return;
+    if (row_ptr[i] > cap) row_ptr[i] = (int)cap;
+    if (i == 0) {
+        flags[FLAG_EDGE_OVERFLOW] = 1;
+        atomicMax(flags + FLAG_EDGE_NEED, total);
+    }
+}
+
+// Reverse edge of every edge e < row_ptr[n] (launched over the capacity).
+__global__ void reverse_kernel(int64_t n, int64_t cap, const int* __restrict__ row_ptr, const int* __restrict__ dst,
                                const int* __restrict__ src, const int* __restrict__ shift,
-                               int* __restrict__ rev, int* __restrict__ flags) {
+                               int* __restrict__ rev, int* __restrict__ flags, const int* cond) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n_edges) return;
+    if (e >= cap || skip(cond) || e >= row_ptr[n]) return;
     const int v = dst[e], w = src[e];
     const int s0 = -shift[e * 3], s1 = -shift[e * 3 + 1], s2 = -shift[e * 3 + 2];
     int found = -1;
@@ -324,7 +351,8 @@ static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t -
 
 sevennet_status build_neighbors(sevennet_model* M, Workspace* ws, const BatchHost& b,
                                 const double* pos_dev, const int32_t* species_dev,
-                                cudaStream_t st, int64_t* n_edges_out, double r_list) {
+                                cudaStream_t st, int64_t* n_edges_out, double r_list, const int* cond,
+                                bool async) {
     const int S = b.n_structs;
     const int64_t N = b.atom_off[S];
     const double rc = r_list > 0.0 ? r_list : M->cfg.r_cut;
@@ -360,7 +388,8 @@ sevennet_status build_neighbors(sevennet_model* M, Workspace* ws, const BatchHos
         n_bins += nb;
     }
     SN_CHECK(n_bins < (1LL << 30), SEVENNET_EINVAL, "too many cell-list bins");
-    int64_t cap_e = std::max<int64_t>(ws->cap_edges, std::max<int64_t>(N * 64, 1024));
+    int64_t cap_e = async ? ws->cap_edges : std::max<int64_t>(ws->cap_edges, std::max<int64_t>(N * 64, 1024));
+    SN_CHECK(!async || cap_e > 0, SEVENNET_EINVAL, "internal error: asynchronous build without edge capacity");
     SN_TRY(ws_reserve(M, ws, N, cap_e, n_bins, S, st));
     SN_CUDA(cudaMemcpyAsync(ws->sdesc, sdesc.data(), sdesc.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     SN_CUDA(cudaMemcpyAsync(ws->cells, b.cells.data(), (size_t)S * 9 * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -368,37 +397,43 @@ sevennet_status build_neighbors(sevennet_model* M, Workspace* ws, const BatchHos
     SN_CUDA(cudaMemcpyAsync(ws->atom_off, b.atom_off.data(), (size_t)(S + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     SN_CUDA(cudaMemsetAsync(ws->bin_count, 0, (size_t)(n_bins + 1) * sizeof(int), st));
     SN_CUDA(cudaMemsetAsync(ws->bin_fill, 0, (size_t)(n_bins + 1) * sizeof(int), st));
-    SN_CUDA(cudaMemsetAsync(ws->flags, 0, 8 * sizeof(int), st));
+    if (!async) SN_CUDA(cudaMemsetAsync(ws->flags, 0, FLAG_WORDS * sizeof(int), st));
     if (N > 0) {
         bin_atoms_kernel<<<blocks_for(N, 256), 256, 0, st>>>(N, S, ws->atom_off, ws->sdesc, ws->inv_cells,
-                                                            pos_dev, ws->bin_of, ws->bin_count);
+                                                            pos_dev, ws->bin_of, ws->bin_count, cond);
     }
-    scan_kernel<<<1, 1024, 0, st>>>(ws->bin_count, n_bins, ws->bin_start, nullptr);
+    scan_kernel<<<1, 1024, 0, st>>>(ws->bin_count, n_bins, ws->bin_start, nullptr, cond);
     if (N > 0) {
-        place_kernel<<<blocks_for(N, 256), 256, 0, st>>>(N, ws->bin_of, ws->bin_start, ws->bin_fill, ws->perm);
-        sort_bins_kernel<<<blocks_for(n_bins, 128), 128, 0, st>>>(n_bins, ws->bin_start, ws->perm);
+        place_kernel<<<blocks_for(N, 256), 256, 0, st>>>(N, ws->bin_of, ws->bin_start, ws->bin_fill, ws->perm,
+                                                        cond);
+        sort_bins_kernel<<<blocks_for(n_bins, 128), 128, 0, st>>>(n_bins, ws->bin_start, ws->perm, cond);
         gather_kernel<<<blocks_for(N, 256), 256, 0, st>>>(N, S, ws->atom_off, ws->sdesc, ws->cells,
                                                          ws->inv_cells, ws->perm, pos_dev, species_dev,
                                                          ws->pos_s, ws->frac_floor, ws->q32, ws->species_s,
-                                                         ws->struct_of);
+                                                         ws->struct_of, cond);
         edges_kernel<false><<<blocks_for(N * NGL, 128), 128, 0, st>>>(
             N, rc * rc, (float)rc, 0, ws->sdesc, ws->cells, ws->struct_of, ws->bin_start, ws->pos_s, ws->q32,
-            ws->frac_floor, nullptr, ws->row_cnt, ws->flags, nullptr, nullptr, nullptr, nullptr);
+            ws->frac_floor, nullptr, ws->row_cnt, ws->flags, nullptr, nullptr, nullptr, nullptr, cond);
     }
-    scan_kernel<<<1, 1024, 0, st>>>(ws->row_cnt, N, ws->row_ptr, ws->flags + 0);
-    SN_CUDA(cudaMemcpyAsync(ws->flags_host, ws->flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    SN_CUDA(cudaStreamSynchronize(st));
-    const int64_t E = ws->flags_host[0];
-    SN_CHECK(ws->flags_host[1] == 0, SEVENNET_EINVAL, "two atoms closer than 1e-8 A");
-    if (E > ws->cap_edges) SN_TRY(ws_reserve(M, ws, N, E + E / 4 + 1024, n_bins, S, st));
+    scan_kernel<<<1, 1024, 0, st>>>(ws->row_cnt, N, ws->row_ptr, ws->flags + 0, cond);
+    int64_t E = -1;                                      // asynchronous: the count stays on the device
+    if (!async) {
+        SN_CUDA(cudaMemcpyAsync(ws->flags_host, ws->flags, FLAG_WORDS * sizeof(int), cudaMemcpyDeviceToHost, st));
+        SN_CUDA(cudaStreamSynchronize(st));
+        E = ws->flags_host[0];
+        SN_CHECK(ws->flags_host[1] == 0, SEVENNET_EINVAL, "two atoms closer than 1e-8 A");
+        if (E > ws->cap_edges) SN_TRY(ws_reserve(M, ws, N, E + E / 4 + 1024, n_bins, S, st));
+    }
     if (N > 0) {
         edges_kernel<true><<<blocks_for(N * NGL, 128), 128, 0, st>>>(
             N, rc * rc, (float)rc, ws->cap_edges, ws->sdesc, ws->cells, ws->struct_of, ws->bin_start, ws->pos_s,
-            ws->q32, ws->frac_floor, ws->row_ptr, nullptr, ws->flags, ws->dst, ws->src, ws->shift, ws->geom);
+            ws->q32, ws->frac_floor, ws->row_ptr, nullptr, ws->flags, ws->dst, ws->src, ws->shift, ws->geom, cond);
+        clamp_rows_kernel<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, ws->row_ptr, ws->cap_edges, ws->flags, cond);
     }
-    if (E > 0)
-        reverse_kernel<<<blocks_for(E, 256), 256, 0, st>>>(E, ws->row_ptr, ws->dst, ws->src, ws->shift,
-                                                          ws->rev, ws->flags);
+    const int64_t span = async ? ws->cap_edges : E;
+    if (span > 0)
+        reverse_kernel<<<blocks_for(span, 256), 256, 0, st>>>(N, span, ws->row_ptr, ws->dst, ws->src, ws->shift,
+                                                             ws->rev, ws->flags, cond);
     SN_CUDA(cudaGetLastError());
     *n_edges_out = E;
     return SEVENNET_OK;
@@ -462,26 +497,26 @@ refresh_kernel(int64_t n, double rc2, int64_t cap, const int* __restrict__ perm,
 sevennet_status refresh_neighbors(sevennet_model* M, Workspace* ws, int64_t N, const double* pos_dev,
                                   const int* list_row_ptr, const int* list_src, const int* list_shift,
                                   cudaStream_t st, int64_t* n_edges_out) {
+    // asynchronous: the count stays on the device, the arrays are sized by capacity
     const double rc = M->cfg.r_cut;
-    SN_CUDA(cudaMemsetAsync(ws->flags, 0, 8 * sizeof(int), st));
     if (N > 0)
         refresh_kernel<false><<<blocks_for(N * NGL, 128), 128, 0, st>>>(
             N, rc * rc, 0, ws->perm, pos_dev, ws->cells, list_row_ptr, list_src, list_shift, nullptr,
             ws->row_cnt, nullptr, nullptr, nullptr, nullptr);
-    scan_kernel<<<1, 1024, 0, st>>>(ws->row_cnt, N, ws->row_ptr, ws->flags + 0);
-    SN_CUDA(cudaMemcpyAsync(ws->flags_host, ws->flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    SN_CUDA(cudaStreamSynchronize(st));
-    const int64_t E = ws->flags_host[0];
-    SN_CHECK(E <= ws->cap_edges, SEVENNET_ECUDA, "internal error: refreshed list exceeds the edge capacity");
-    if (N > 0)
+    scan_kernel<<<1, 1024, 0, st>>>(ws->row_cnt, N, ws->row_ptr, ws->flags + 0, nullptr);
+    if (N > 0) {
         refresh_kernel<true><<<blocks_for(N * NGL, 128), 128, 0, st>>>(
             N, rc * rc, ws->cap_edges, ws->perm, pos_dev, ws->cells, list_row_ptr, list_src, list_shift,
             ws->row_ptr, nullptr, ws->dst, ws->src, ws->shift, ws->geom);
-    if (E > 0)
-        reverse_kernel<<<blocks_for(E, 256), 256, 0, st>>>(E, ws->row_ptr, ws->dst, ws->src, ws->shift,
-                                                          ws->rev, ws->flags);
+        clamp_rows_kernel<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, ws->row_ptr, ws->cap_edges, ws->flags,
+                                                                 nullptr);
+    }
+    if (ws->cap_edges > 0)
+        reverse_kernel<<<blocks_for(ws->cap_edges, 256), 256, 0, st>>>(N, ws->cap_edges, ws->row_ptr, ws->dst,
+                                                                      ws->src, ws->shift, ws->rev, ws->flags,
+                                                                      nullptr);
     SN_CUDA(cudaGetLastError());
-    *n_edges_out = E;
+    *n_edges_out = -1;
     return SEVENNET_OK;
 }
 

@@ -43,7 +43,10 @@ static sevennet_status scratch_address(int device, void** out) {
     return SEVENNET_OK;
 }
 
-// Receiver of every edge and (d, |d|), with writes kept inside [0, n_edges).
+// Receiver of every edge and (d, |d|).  The clamp keeps this kernel's own
+// writes inside [0, n_edges); it does not make an invalid CSR safe: the
+// convolution walks the edges by the caller's row_ptr, which must be a valid
+// CSR with row_ptr[n_atoms] == n_edges (as the header states).
 __global__ void noalloc_prepare_kernel(int64_t n_atoms, int64_t n_edges, const int* __restrict__ row_ptr,
                                        const float* __restrict__ d, int* __restrict__ dst,
                                        float4* __restrict__ geom) {

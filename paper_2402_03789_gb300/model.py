@@ -213,11 +213,25 @@ class SevenNet:
         L.check(self.lib.sevennet_conv_dims(self.handle, layer, ctypes.byref(xd), ctypes.byref(md)))
         return xd.value, md.value
 
+    def _check_conv_args(self, layer, row_ptr, src, d, x, g_m=None):
+        import torch
+        xdim, mdim = self.conv_dims(layer)
+        dev = torch.device("cuda", self.device)
+        for name, t, dt in (("row_ptr", row_ptr, torch.int32), ("src", src, torch.int32),
+                            ("d", d, torch.float32), ("x", x, torch.float32), ("g_m", g_m, torch.float32)):
+            if t is None:
+                continue
+            if t.dtype != dt or t.device != dev or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous {dt} tensor on {dev} "
+                                 f"(got {t.dtype} on {t.device}, contiguous={t.is_contiguous()})")
+        n = row_ptr.numel() - 1
+        if d.shape != (src.numel(), 3) or x.shape != (n, xdim) or (g_m is not None and g_m.shape != (n, mdim)):
+            raise ValueError("shapes: d [E, 3], x [n_atoms, x_dim] and g_m [n_atoms, m_dim] expected")
+        return n, src.numel(), mdim
+
     def conv_forward(self, layer, row_ptr, src, d, x, precision="fp32", stream=None):
         import torch
-        n = row_ptr.numel() - 1
-        E = src.numel()
-        _, mdim = self.conv_dims(layer)
+        n, E, mdim = self._check_conv_args(layer, row_ptr, src, d, x)
         m = torch.empty((n, mdim), dtype=torch.float32, device=x.device)
         L.check(self.lib.sevennet_conv_forward_dev(
             self.handle, layer, n, E, ctypes.c_void_p(row_ptr.data_ptr()), ctypes.c_void_p(src.data_ptr()),
@@ -227,8 +241,7 @@ class SevenNet:
 
     def conv_backward(self, layer, row_ptr, src, d, x, g_m, precision="fp32", stream=None):
         import torch
-        n = row_ptr.numel() - 1
-        E = src.numel()
+        n, E, _ = self._check_conv_args(layer, row_ptr, src, d, x, g_m)
         g_x = torch.empty_like(x)
         g_d = torch.zeros((E, 3), dtype=torch.float32, device=x.device)
         L.check(self.lib.sevennet_conv_backward_dev(

@@ -2,8 +2,10 @@
 not allocate device memory during the call.  Its scratch is a static device
 array of the library, so this checks, through the C ABI, that two calls in a
 row give the same messages as sevennet_conv_forward_dev (the allocating entry
-point) within the FP32 tolerance used by the other convolution tests, and that
-sizes beyond its fixed scratch are refused."""
+point; both run the same kernel, so bit for bit) in both precisions, that the
+calls take nothing from the device's stream-ordered memory pool (which the
+allocating entry point does use), and that sizes beyond its fixed scratch are
+refused."""
 
 import ctypes
 
@@ -37,31 +39,64 @@ def _inputs(spec, layer, seed):
             torch.tensor(x, dtype=torch.float32, device=dev))
 
 
-def _call(lib, fn, model, layer, n, E, rp, src, d, x, mdim):
+def _call(lib, fn, model, layer, n, E, rp, src, d, x, mdim, prec):
     m = torch.full((n, mdim), float("nan"), dtype=torch.float32, device="cuda")
     st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     rc = getattr(lib, fn)(model.handle, layer, n, E, ctypes.c_void_p(rp.data_ptr()),
                           ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(d.data_ptr()),
-                          ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(m.data_ptr()), 0, st)
+                          ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(m.data_ptr()), prec, st)
     return rc, m
 
 
-def test_noalloc_forward_matches_allocating_entry_point_twice():
+class _Pool:
+    """The device's default stream-ordered memory pool (driver API), whose
+    used-memory high-water mark shows whether a call allocated from it."""
+    USED_MEM_CURRENT, USED_MEM_HIGH = 7, 8      # CUmemPool_attribute
+
+    def __init__(self):
+        self.cu = ctypes.CDLL("libcuda.so.1")
+        dev = ctypes.c_int()
+        assert self.cu.cuDeviceGet(ctypes.byref(dev), torch.cuda.current_device()) == 0
+        self.pool = ctypes.c_void_p()
+        assert self.cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
+
+    def get(self, attr):
+        v = ctypes.c_uint64()
+        assert self.cu.cuMemPoolGetAttribute(self.pool, attr, ctypes.byref(v)) == 0
+        return v.value
+
+    def reset_high(self):
+        torch.cuda.synchronize()
+        z = ctypes.c_uint64(0)
+        assert self.cu.cuMemPoolSetAttribute(self.pool, self.USED_MEM_HIGH, ctypes.byref(z)) == 0
+        return self.get(self.USED_MEM_CURRENT)
+
+    def grew(self, base):
+        torch.cuda.synchronize()
+        return self.get(self.USED_MEM_HIGH) > base
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_noalloc_forward_matches_allocating_entry_point_twice(prec):
     from paper_2402_03789_gb300 import _lib
     lib = _lib.load()
     spec = MODEL_SEVENNET0
     model = get_model(spec)
+    pool = _Pool()
     for layer, seed in [(2, 61), (0, 62)]:          # two calls in a row
         n, E, rp, src, d, x = _inputs(spec, layer, seed)
         mdim = model.conv_dims(layer)[1]
-        rc, m_ref = _call(lib, "sevennet_conv_forward_dev", model, layer, n, E, rp, src, d, x, mdim)
+        base = pool.reset_high()
+        rc, m_ref = _call(lib, "sevennet_conv_forward_dev", model, layer, n, E, rp, src, d, x, mdim, prec)
         assert rc == 0
-        rc, m_new = _call(lib, "sevennet_conv_forward_noalloc", model, layer, n, E, rp, src, d, x, mdim)
+        assert pool.grew(base)                       # the allocating entry point takes pool memory
+        base = pool.reset_high()
+        rc, m_new = _call(lib, "sevennet_conv_forward_noalloc", model, layer, n, E, rp, src, d, x, mdim, prec)
         assert rc == 0
-        torch.cuda.synchronize()
+        assert not pool.grew(base)                   # this one does not
         a, b = m_new.cpu().numpy(), m_ref.cpu().numpy()
         assert np.all(np.isfinite(a))
-        assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 1e-5
+        assert np.array_equal(a, b)
 
 
 def test_noalloc_refuses_sizes_beyond_its_scratch():
