@@ -124,7 +124,23 @@ int64_t sevennet_n_params(const sevennet_model_config* cfg);
 
 /* Build a model on CUDA device `device` from the canonical FP64 weight vector
  * (length n_weights = sevennet_n_params(cfg); copied, converted to FP32 and
- * BF16 device copies).  Paper Sec. 5.1 (hyper-parameters), Figure 2 (blocks). */
+ * BF16 device copies).  Paper Sec. 5.1 (hyper-parameters), Figure 2 (blocks).
+ * Multiplicities cfg->mul[l] may be any value in [1, 256] (the 4-64 channel
+ * models of Sec. 4); those that are not multiples of 32 run as the exact
+ * zero-padded model of sevennet_padded_weights (same energy, forces and
+ * virial; normalised by the true fan-in). */
+/* Host only (no GPU needed): the model the library runs for cfg.  Each
+ * multiplicity is rounded up to a multiple of 32 (written to mul_out[4], unused
+ * entries 0) and the canonical weights are copied into the padded layout with
+ * zeros for the added channels; the linears (self-connection, linear_1,
+ * linear_2, readout) are multiplied by sqrt(padded fan-in / true fan-in), so the
+ * library's 1/sqrt(fan-in) of the padded model equals the true one.  The added
+ * channels stay zero through every operation, so the padded model is exact.
+ * out (may be NULL) receives the padded vector, n_out entries (the
+ * sevennet_n_params of the padded configuration).  EINVAL for a bad config, a
+ * wrong n_weights or a wrong n_out. */
+sevennet_status sevennet_padded_weights(const sevennet_model_config* cfg, const double* weights,
+                                        size_t n_weights, int32_t* mul_out, double* out, size_t n_out);
 sevennet_status sevennet_create_model(const sevennet_model_config* cfg,
                                       const double* weights, size_t n_weights,
                                       int device, sevennet_model** out);

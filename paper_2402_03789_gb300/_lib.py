@@ -71,6 +71,7 @@ _IP = ctypes.POINTER(ctypes.c_int32)
 SIGNATURES = {
     "sevennet_last_error": (ctypes.c_char_p, []),
     "sevennet_n_params": (_I64, [ctypes.POINTER(ModelConfig)]),
+    "sevennet_padded_weights": (_I32, [ctypes.POINTER(ModelConfig), _D, ctypes.c_size_t, _IP, _D, ctypes.c_size_t]),
     "sevennet_create_model": (_I32, [ctypes.POINTER(ModelConfig), _D, ctypes.c_size_t, ctypes.c_int,
                                      ctypes.POINTER(_P)]),
     "sevennet_destroy_model": (None, [_P]),

@@ -100,7 +100,7 @@ static bool config_valid(const sevennet_model_config* c, std::string* why) {
     if (c->lmax < 1 || c->lmax > MAX_LMAX) return fail("lmax must be 1, 2 or 3");
     if (c->lmax == 3 && c->mlp_hidden != 64) return fail("lmax 3 models need mlp_hidden 64");
     for (int l = 0; l <= c->lmax; ++l)
-        if (c->mul[l] < 32 || c->mul[l] % 32 || c->mul[l] > 256) return fail("mul[l] must be a multiple of 32 in [32, 256]");
+        if (c->mul[l] < 1 || c->mul[l] > 256) return fail("mul[l] must be in [1, 256]");
     if (!(c->r_cut > 0) || !std::isfinite(c->r_cut)) return fail("r_cut must be positive");
     if (c->n_basis < 1 || c->n_basis > MAX_NB) return fail("n_basis must be in [1, 16]");
     if (c->poly_p < 1 || c->poly_p > 32) return fail("poly_p must be in [1, 32]");
@@ -172,6 +172,99 @@ static std::vector<WEntry> weight_entries(const sevennet_model_config* c) {
     add("readout0", c->mul[0], c->readout_hidden);
     add("readout1", c->readout_hidden, 1);
     return e;
+}
+
+// ---------------------------------------------------------------- small multiplicities
+// The kernels give a warp 32 channels of an irrep, so a model whose multiplicity
+// of some irrep is not a multiple of 32 (the 4-16 channel models of Sec. 4) runs
+// as the model with every multiplicity rounded up to a multiple of 32 and the
+// added channels' weights zero.  A zero channel stays zero through every
+// operation (linear rows and columns, radial-MLP output columns, SiLU(0) = 0
+// gates, readout rows), so energy, forces and virial are those of the original
+// model.  The linears are normalised by the true fan-in: the library scales by
+// 1/sqrt(padded fan-in), so the copied weights are multiplied by
+// sqrt(padded fan-in / true fan-in).
+static int pad32(int m) { return (m + 31) / 32 * 32; }
+
+struct PadEntry {
+    std::vector<int> rs, cs;    // true row / column segments (each padded separately)
+    bool map_rows, map_cols;    // false: identity (sizes that are not multiplicities)
+    bool fan_rows;              // normalised by 1/sqrt(rows)
+};
+
+static std::vector<PadEntry> pad_entries(const sevennet_model_config* c) {
+    std::vector<PadEntry> e;
+    const int H = c->mlp_hidden;
+    e.push_back({{c->n_species}, {c->mul[0]}, false, true, false});                 // embed
+    for (int t = 0; t < c->n_layers; ++t) {
+        int in_mul[NL], y_mul[NL], out_mul[NL], msg_mul[NL];
+        std::vector<PathH> paths;
+        bool last;
+        block_irreps(c, t, in_mul, y_mul, out_mul, paths, msg_mul, &last);
+        auto yseg = [&](int l) {
+            std::vector<int> v;
+            if (l == 0 && !last) for (int k = 0; k <= c->lmax; ++k) v.push_back(c->mul[k]);   // scalars, gates
+            else v.push_back(y_mul[l]);
+            return v;
+        };
+        for (int l = 0; l < NL; ++l)
+            if (y_mul[l] && in_mul[l]) e.push_back({{in_mul[l]}, yseg(l), true, true, true});      // sc
+        for (int l = 0; l < NL; ++l)
+            if (in_mul[l]) e.push_back({{in_mul[l]}, {in_mul[l]}, true, true, true});            // lin1
+        std::vector<int> wseg;
+        for (auto& q : paths) wseg.push_back(q.mul);
+        e.push_back({{c->n_basis}, {H}, false, false, false});                                   // mlp0
+        e.push_back({{H}, {H}, false, false, false});                                            // mlp1
+        e.push_back({{H}, wseg, false, true, false});                                            // mlp2
+        for (int l = 0; l < NL; ++l)
+            if (y_mul[l] && msg_mul[l]) {
+                std::vector<int> mseg;
+                for (auto& q : paths) if (q.l3 == l) mseg.push_back(q.mul);
+                e.push_back({mseg, yseg(l), true, true, true});                                  // lin2
+            }
+    }
+    e.push_back({{c->mul[0]}, {c->readout_hidden}, true, false, true});                         // readout0
+    e.push_back({{c->readout_hidden}, {1}, false, false, false});                               // readout1
+    return e;
+}
+
+static std::vector<int64_t> pad_index(const std::vector<int>& segs, bool map) {
+    std::vector<int64_t> idx;
+    int64_t base = 0;
+    for (int s : segs) {
+        for (int i = 0; i < s; ++i) idx.push_back(base + i);
+        base += map ? pad32(s) : s;
+    }
+    return idx;
+}
+
+// The padded configuration and its canonical weight vector.
+static void pad_model(const sevennet_model_config* c, sevennet_model_config* pc, const double* w,
+                      std::vector<double>* wp) {
+    *pc = *c;
+    for (int l = 0; l <= c->lmax; ++l) pc->mul[l] = pad32(c->mul[l]);
+    const auto et = pad_entries(c), ep = pad_entries(pc);
+    size_t np = 0;
+    for (const auto& e : ep) {
+        int64_t R = 0, C = 0;
+        for (int r : e.rs) R += r;
+        for (int k : e.cs) C += k;
+        np += (size_t)(R * C);
+    }
+    wp->assign(np, 0.0);
+    int64_t ot = 0, op = 0;
+    for (size_t k = 0; k < et.size(); ++k) {
+        const auto ri = pad_index(et[k].rs, et[k].map_rows), ci = pad_index(et[k].cs, et[k].map_cols);
+        int64_t Rp = 0, Cp = 0;
+        for (int r : ep[k].rs) Rp += r;
+        for (int x : ep[k].cs) Cp += x;
+        const double sc = et[k].fan_rows ? std::sqrt((double)Rp / (double)ri.size()) : 1.0;
+        for (size_t i = 0; i < ri.size(); ++i)
+            for (size_t j = 0; j < ci.size(); ++j)
+                (*wp)[op + ri[i] * Cp + ci[j]] = w[ot + (int64_t)i * (int64_t)ci.size() + (int64_t)j] * sc;
+        ot += (int64_t)ri.size() * (int64_t)ci.size();
+        op += Rp * Cp;
+    }
 }
 
 // ---------------------------------------------------------------- device upload
@@ -595,6 +688,25 @@ extern "C" {
 
 const char* sevennet_last_error(void) { return sn::g_last_error.c_str(); }
 
+sevennet_status sevennet_padded_weights(const sevennet_model_config* cfg, const double* weights, size_t n_weights,
+                                        int32_t* mul_out, double* out, size_t n_out) {
+    std::string why;
+    SN_CHECK(config_valid(cfg, &why), SEVENNET_EINVAL, "%s", why.c_str());
+    const int64_t need = sevennet_n_params(cfg);
+    SN_CHECK(weights && (int64_t)n_weights == need, SEVENNET_EINVAL,
+             "weight vector has %zu entries, the model needs %lld", n_weights, (long long)need);
+    sevennet_model_config pc;
+    std::vector<double> wp;
+    pad_model(cfg, &pc, weights, &wp);
+    if (mul_out) for (int l = 0; l < 4; ++l) mul_out[l] = pc.mul[l];
+    if (out) {
+        SN_CHECK(n_out == wp.size(), SEVENNET_EINVAL, "output has %zu entries, the padded model has %zu", n_out,
+                 wp.size());
+        std::copy(wp.begin(), wp.end(), out);
+    }
+    return SEVENNET_OK;
+}
+
 int64_t sevennet_n_params(const sevennet_model_config* cfg) {
     std::string why;
     if (!config_valid(cfg, &why)) {
@@ -616,6 +728,16 @@ sevennet_status sevennet_create_model(const sevennet_model_config* cfg, const do
              "weight vector has %zu entries, the model needs %lld", n_weights, (long long)need);
     for (size_t i = 0; i < n_weights; ++i)
         SN_CHECK(std::isfinite(weights[i]), SEVENNET_EINVAL, "weight %zu is not finite", i);
+    // multiplicities that are not multiples of 32 run as the exact zero-padded model
+    sevennet_model_config padded;
+    std::vector<double> wpad;
+    bool pad = false;
+    for (int l = 0; l <= cfg->lmax; ++l) pad |= (cfg->mul[l] % 32) != 0;
+    if (pad) {
+        pad_model(cfg, &padded, weights, &wpad);
+        cfg = &padded;
+        weights = wpad.data();
+    }
     int ndev = 0;
     SN_CUDA(cudaGetDeviceCount(&ndev));
     SN_CHECK(device >= 0 && device < ndev, SEVENNET_EINVAL, "device %d out of range (%d devices)", device, ndev);

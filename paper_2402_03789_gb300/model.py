@@ -10,7 +10,6 @@ import ctypes
 import numpy as np
 
 from . import _lib as L
-from . import padding
 
 
 def make_config(spec, shift=None):
@@ -43,13 +42,30 @@ def make_config(spec, shift=None):
 
 
 def n_params(spec) -> int:
-    if not isinstance(spec, dict) and padding.needs_padding(spec):
-        return padding.n_params(spec)
     c, _keep = make_config(spec)
     n = L.load().sevennet_n_params(ctypes.byref(c))
     if n < 0:
         L.check(L.EINVAL)
     return int(n)
+
+
+def padded_model(spec, weights):
+    """(padded multiplicities, padded canonical weights) of the exact
+    zero-padded model the library runs (sevennet_padded_weights; host only)."""
+    lib = L.load()
+    c, _keep = make_config(spec)
+    w = L.as_f64(weights).reshape(-1)
+    mul = (ctypes.c_int32 * 4)()
+    L.check(lib.sevennet_padded_weights(ctypes.byref(c), L.dptr(w), w.size, mul, None, 0))
+    cp, _kp = make_config(spec)
+    for l in range(4):
+        cp.mul[l] = mul[l]
+    n = lib.sevennet_n_params(ctypes.byref(cp))
+    if n < 0:
+        L.check(L.EINVAL)
+    out = np.zeros(int(n))
+    L.check(lib.sevennet_padded_weights(ctypes.byref(c), L.dptr(w), w.size, mul, L.dptr(out), out.size))
+    return tuple(int(mul[l]) for l in range(4) if mul[l]), out
 
 
 def _prec(p):
@@ -73,9 +89,6 @@ class SevenNet:
 
     def __init__(self, spec, weights, device: int = 0):
         self.lib = L.load()
-        if not isinstance(spec, dict) and padding.needs_padding(spec):
-            # fewer than 32 channels of some irrep: the exact zero-padded model
-            spec, weights = padding.pad_model(spec, weights)
         cfg, keep = make_config(spec)
         self._cfg = cfg
         self._keep = keep

@@ -49,38 +49,45 @@ def test_invalid_config_rejected(lib):
     import ctypes
     import paper_2402_03789_gb300 as sn
     from paper_2402_03789_gb300.model import make_config
-    # the C ABI takes multiplicities that are multiples of 32 only (the Python
-    # binding pads smaller ones, exactly); a radial MLP width of 48 is invalid
-    c, _keep = make_config(dataclasses.replace(MODEL_TINY, mul=(30, 32)))
+    # a multiplicity of 0 or above 256 and a radial MLP width of 48 are invalid
+    c, _keep = make_config(dataclasses.replace(MODEL_TINY, mul=(0, 32)))
+    assert lib.sevennet_n_params(ctypes.byref(c)) < 0
+    c, _keep = make_config(dataclasses.replace(MODEL_TINY, mul=(32, 288)))
     assert lib.sevennet_n_params(ctypes.byref(c)) < 0
     with pytest.raises(sn.SevenNetError):
         sn.n_params(dataclasses.replace(MODEL_TINY, mlp_hidden=48))
 
 
-def test_padding_walker_matches_oracle_layout():
-    # models with fewer than 32 channels run zero-padded: the binding's walk of
-    # the canonical weight layout must count exactly the oracle's parameters
+def _small_specs():
     import dataclasses
-    import oracle
-    from synth import MODEL_SEVENNET0, benchmark_model
-    from paper_2402_03789_gb300 import padding
-    for spec in (benchmark_model(3, 8, lmax=3), benchmark_model(2, 4), benchmark_model(5, 16, lmax=3),
-                 dataclasses.replace(MODEL_SEVENNET0, mul=(48, 16, 8))):
-        assert padding.n_params(spec) == oracle.n_params(spec)
-        spec_p, w_p = padding.pad_model(spec, np.arange(oracle.n_params(spec), dtype=np.float64))
-        assert all(m % 32 == 0 for m in spec_p.mul)
-        assert w_p.size == oracle.n_params(spec_p)
+    from synth import benchmark_model
+    return (benchmark_model(3, 8, lmax=3), benchmark_model(2, 4), benchmark_model(5, 16, lmax=3),
+            dataclasses.replace(MODEL_SEVENNET0, mul=(48, 16, 8)))
 
 
-def test_padded_model_is_exact_in_the_oracle():
-    # zero-padding a small-channel model to multiples of 32 leaves E, F and W
-    # unchanged: the padded channels stay zero through every operation
+def test_small_multiplicities_count_like_the_oracle(lib):
+    # any multiplicity in [1, 256] is accepted and counted in the canonical (unpadded) layout
+    import paper_2402_03789_gb300 as sn
+    for spec in _small_specs():
+        assert sn.n_params(spec) == oracle.n_params(spec)
+
+
+def test_library_padding_is_exact_in_the_oracle(lib):
+    # the library runs a model with multiplicities that are not multiples of 32
+    # as the zero-padded model of sevennet_padded_weights; in the FP64 oracle the
+    # padded model has the same E, F and W (the added channels stay zero) and the
+    # padded vector has the padded configuration's parameter count
+    import dataclasses
     from synth import benchmark_model, make_quartz, normal_weights
-    from paper_2402_03789_gb300 import padding
+    from paper_2402_03789_gb300.model import padded_model
     s = make_quartz("quartz_216")
-    for spec in (benchmark_model(2, 8, lmax=2), benchmark_model(2, 4, lmax=3)):
+    for spec in (benchmark_model(2, 8, lmax=2), benchmark_model(2, 4, lmax=3),
+                 dataclasses.replace(MODEL_TINY, mul=(20, 12))):
         w = normal_weights(oracle.n_params(spec))
-        spec_p, w_p = padding.pad_model(spec, w)
+        mul_p, w_p = padded_model(spec, w)
+        assert all(m % 32 == 0 for m in mul_p) and len(mul_p) == len(spec.mul)
+        spec_p = dataclasses.replace(spec, mul=mul_p)
+        assert w_p.size == oracle.n_params(spec_p)
         E, F, W, *_ = oracle.energy_forces_virial(spec, w, s.species, s.pos, s.cell)
         Ep, Fp, Wp, *_ = oracle.energy_forces_virial(spec_p, w_p, s.species, s.pos, s.cell)
         assert abs(Ep - E) <= 1e-9 * max(1.0, abs(E))

@@ -33,7 +33,8 @@ def test_benchmark_shape_matches_oracle(n_layers, channels, lmax):
 
 @pytest.mark.parametrize("n_layers,channels,lmax", [(2, 4, 3), (3, 8, 3), (3, 16, 2)])
 def test_small_channel_models_match_oracle(n_layers, channels, lmax):
-    # the paper's 4-16 channel models run as the exact zero-padded 32-channel model
+    # the paper's 4-16 channel models, created through the C ABI from their own
+    # (unpadded) weights; the library runs them as the exact zero-padded model
     s = make_quartz("quartz_216")
     spec = benchmark_model(n_layers, channels, lmax=lmax)
     import paper_2402_03789_gb300 as sn
