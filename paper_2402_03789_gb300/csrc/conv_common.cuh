@@ -71,7 +71,10 @@ __host__ __device__ inline ConvSmem conv_smem_layout(int Wpad, int WpadB, int H,
     int o = 0;
     const int stage_bf = H * EC > MAX_NB * EC ? H * EC : MAX_NB * EC;
     const int stage_f32 = KS * DCOLS > 2 * CS * 64 ? KS * DCOLS : 2 * CS * 64;
-    s.w = o;     o += (bf && !bwd) ? EC * WpadB / 2 : EC * Wpad;   // [EC][row stride]: BF16 in the BF16 forward
+    // [EC][row stride]: BF16 in the BF16 forward; the BF16 adjoint also keeps three
+    // [H][EC] partials of phase F there
+    const int w_bwd_bf = EC * Wpad > 3 * H * EC ? EC * Wpad : 3 * H * EC;
+    s.w = o;     o += (bf && !bwd) ? EC * WpadB / 2 : (bf ? w_bwd_bf : EC * Wpad);
     s.stage = o; o += bf ? stage_bf : (stage_f32 > stage_bf ? stage_f32 : stage_bf);
     s.A1 = o;    o += H * EC;
     s.A2 = o;    o += H * EC;
@@ -309,39 +312,34 @@ __device__ __forceinline__ void chunk_w_gemm_bf16(const ConvDesc& D, const ConvS
 }
 
 // Phase F (BF16): gH2[k][e] = sum_c gw[e][c] W3[k][c]; B operand W3 [H][W] (bf16).
-// K (the W columns, in blocks of 32) is split between two groups of four warps;
-// within a group each warp owns H/32 n tiles of 8 hidden units for its whole K
-// half, so every output has one writer per group.  Group 0 writes dE/dH2,
-// group 1 a partial in the staging region, and the two are added in a fixed
-// order: the result does not depend on the warps' timing.
+// K (the W columns, in blocks of 32) is split between four groups of two warps;
+// within a group each warp owns H/16 n tiles of 8 hidden units for the group's
+// whole K range, so every output has one writer per group.  Group 0 writes
+// dE/dH2; groups 1-3 write partials into the dE/dw tile once every warp is done
+// reading it (the BF16 adjoint's tile holds at least three [H][EC] partials),
+// and the partials are added in group order, so the result does not depend on
+// the warps' timing.
 template <int H>
 __device__ __forceinline__ void chunk_gw_gemm_bf16(const ConvDesc& D, const ConvSmem& L, float* smem,
                                                    const __nv_bfloat16* __restrict__ W3h) {
-    constexpr int NTW = H / 32;                // n tiles per warp (2 or 1)
+    constexpr int G = 4, WPG = CONV_WARPS / G;
+    constexpr int NTW = (H / 8) / WPG;         // n tiles per warp (4 or 2)
     static_assert(EC == 16, "one m tile of edges");
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tq = lane & 3;
-    const int grp = warp >> 2, wq = warp & 3;
-    const float* s_w = smem + L.w;             // dE/dw, [EC][Wpad]
+    const int grp = warp / WPG, wq = warp % WPG;
+    float* s_w = smem + L.w;                   // dE/dw, [EC][Wpad]
     float* s_gH = smem + L.gH;                 // [H][EC]
-    float* s_part = smem + L.stage;            // group 1's partial, same layout
     const int W = D.W, nkb = W / 32;
-    const int kb0 = grp ? nkb / 2 : 0, kb1 = grp ? nkb : nkb / 2;
+    const int kb0 = nkb * grp / G, kb1 = nkb * (grp + 1) / G;
     __syncthreads();                           // every warp's dE/dw of phase E is in s_w
     float c[NTW][4];
 #pragma unroll
     for (int j = 0; j < NTW; ++j) c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
-    uint4 bn[NTW];
-    auto load_b = [&](int kb) {
-#pragma unroll
-        for (int j = 0; j < NTW; ++j)
-            bn[j] = __ldg(reinterpret_cast<const uint4*>(W3h + (size_t)((wq * NTW + j) * 8 + g) * W + kb * 32) + tq);
-    };
-    if (kb0 < kb1) load_b(kb0);
     for (int kb = kb0; kb < kb1; ++kb) {
         uint4 bv[NTW];
 #pragma unroll
-        for (int j = 0; j < NTW; ++j) bv[j] = bn[j];
-        if (kb + 1 < kb1) load_b(kb + 1);
+        for (int j = 0; j < NTW; ++j)
+            bv[j] = __ldg(reinterpret_cast<const uint4*>(W3h + (size_t)((wq * NTW + j) * 8 + g) * W + kb * 32) + tq);
         // k step ks covers words kb*16 + 4 tq + 2 ks (+1): columns 32 kb + 8 tq + 4 ks .. + 3
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) {
@@ -358,7 +356,8 @@ __device__ __forceinline__ void chunk_gw_gemm_bf16(const ConvDesc& D, const Conv
             }
         }
     }
-    float* out = grp ? s_part : s_gH;
+    __syncthreads();                           // the partials overwrite s_w
+    float* out = grp == 0 ? s_gH : s_w + (grp - 1) * H * EC;
 #pragma unroll
     for (int j = 0; j < NTW; ++j) {
         const int k = (wq * NTW + j) * 8 + 2 * tq;
@@ -368,7 +367,8 @@ __device__ __forceinline__ void chunk_gw_gemm_bf16(const ConvDesc& D, const Conv
         out[hk<H>(k + 1, g + 8)] = c[j][3];
     }
     __syncthreads();
-    for (int i = t; i < H * EC; i += CONV_THREADS) s_gH[i] += s_part[i];
+    for (int i = t; i < H * EC; i += CONV_THREADS)
+        s_gH[i] = ((s_gH[i] + s_w[i]) + s_w[H * EC + i]) + s_w[2 * H * EC + i];
     __syncthreads();
 }
 
