@@ -21,7 +21,7 @@
 
 namespace sn {
 
-constexpr int TC_WS = 18;       // BF16 values between two columns of the [W][edge] weight tile
+constexpr int TC_WS = 24;       // BF16 values between two columns of the [W][edge] weight tile (48 bytes: conflict-free lane patterns)
 constexpr int TC_XPIECES = 6;   // 16-byte pieces of an x row per lane (x rows of at most 768 floats)
 
 struct TcSmem {
