@@ -583,7 +583,7 @@ void model_layer_forward(sevennet_model* M, Workspace* ws, int t, int64_t N, int
     }
     run_gemm(M, g, prec, st);
     prof_begin(P, PF_CONV_FWD, st, &ev);
-    launch_conv_fwd(L, M->H, prec, N, E, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m, st);
+    launch_conv_fwd(L, M->H, prec, N, E, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m, st, ws->flags);
     prof_end(P, PF_CONV_FWD, st, ev, 1);
     count_launches(1);
     GemmBatch g2{};
@@ -1000,6 +1000,7 @@ sevennet_status check_flags(const int* f) {
              "a feature gradient in the convolution adjoint reached 2^16 (outside the fixed-point range)");
     SN_CHECK(f[FLAG_EDGE_OVERFLOW] == 0, SEVENNET_EOVERFLOW, "neighbour list larger than its capacity");
     SN_CHECK(f[2] == 0, SEVENNET_ECUDA, "internal error: reverse edge not found");
+    SN_CHECK(f[FLAG_COPY_TIMEOUT] == 0, SEVENNET_ETIMEDOUT, "a bulk copy did not complete within its bounded wait");
     return SEVENNET_OK;
 }
 

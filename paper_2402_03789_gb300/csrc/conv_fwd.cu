@@ -269,13 +269,13 @@ sevennet_status conv_configure_fwd(int H, size_t need) {
 
 void launch_conv_fwd(const LayerDev& L, int H, sevennet_precision prec, int64_t n_atoms,
                      int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
-                     const float4* geom, const float* x, float* m, cudaStream_t st) {
+                     const float4* geom, const float* x, float* m, cudaStream_t st, int* flags) {
     const int lm = L.conv.lmax;
     const bool bf = prec == SEVENNET_BF16;
     // BF16: the tensor-core contraction (conv_fwd_tc.cu) where the block allows
-    // it; its cp.async staging wants 16-byte aligned x rows
+    // it; its bulk copies of the x rows want 16-byte aligned rows
     if (bf && L.conv.tc_ok && (reinterpret_cast<uintptr_t>(x) & 15) == 0) {
-        launch_conv_fwd_tc(L, H, n_atoms, n_edges, row_ptr, dst, src, geom, x, m, st);
+        launch_conv_fwd_tc(L, H, n_atoms, n_edges, row_ptr, dst, src, geom, x, m, flags, st);
         return;
     }
     const int grid = conv_grid(n_atoms, conv_ctas_per_sm(lm));

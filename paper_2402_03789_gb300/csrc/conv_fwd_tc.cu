@@ -14,7 +14,8 @@
 // slots of A zeroed.  The accumulator is written when the receiver changes.
 //
 // Per 16-edge chunk: edge features (FP32), the x rows of the chunk's senders
-// copied to shared memory with cp.async while the radial MLP runs, the B
+// copied to shared memory by bulk copies (cp.async.bulk, completed on an
+// mbarrier) while the radial MLP runs, the B
 // fragments of every path built from Y, the hidden MLP layer and w^T = W3^T H2^T
 // on mma.sync (w kept in BF16 as a [W][edge] tile), then the work units.
 #include "conv_common.cuh"
@@ -22,7 +23,6 @@
 namespace sn {
 
 constexpr int TC_WS = 24;       // BF16 values between two columns of the [W][edge] weight tile (48 bytes: conflict-free lane patterns)
-constexpr int TC_XPIECES = 6;   // 16-byte pieces of an x row per lane (x rows of at most 768 floats)
 
 struct TcSmem {
     int w, xs, bf, stage, H2, Y, B, src, dst, first, W1, total;
@@ -51,10 +51,41 @@ struct TcSets {
     static constexpr PathSets sets = tc_path_sets(L1, LMAX, KIND);
 };
 
-__device__ __forceinline__ void cp_async16(void* s, const void* g) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+// ---- bulk copies (the TMA engine's linear mode) completed on an mbarrier
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(a), "r"(bytes) : "memory");
+}
+
+// global -> shared, `bytes` a multiple of 16 and both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 ::"r"(d), "l"(src), "r"(bytes), "r"(b) : "memory");
+}
+
+// Wait for phase `parity` of the barrier to complete, for at most about `limit`
+// clock cycles; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    const long long t0 = clock64();
+    while (true) {
+        unsigned done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
+constexpr long long TC_WAIT_LIMIT = 4000000000LL;   // about two seconds at 2 GHz
 
 __device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
 __device__ __forceinline__ __nv_bfloat162 bits_bf2(uint32_t v) { return *reinterpret_cast<__nv_bfloat162*>(&v); }
@@ -306,11 +337,14 @@ __global__ void __launch_bounds__(CONV_THREADS, 2)
 conv_fwd_tc_kernel(const ConvDesc D, const float* __restrict__ W1, const __nv_bfloat16* __restrict__ W3T_h,
                    const __nv_bfloat16* __restrict__ W2T_h, int n_atoms, int n_edges,
                    const int* __restrict__ row_ptr, const int* __restrict__ dst, const int* __restrict__ src,
-                   const float4* __restrict__ geom, const float* __restrict__ x, float* __restrict__ m) {
+                   const float4* __restrict__ geom, const float* __restrict__ x, float* __restrict__ m,
+                   int* flags) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
     const TcSmem L = tc_smem_layout(D, H);
     __shared__ int s_range[2];
+    __shared__ __align__(8) uint64_t s_bar;           // completion of the chunk's x-row copies
+    if (threadIdx.x == 0) mbar_init(&s_bar, 1);
     cta_range(n_atoms, n_edges, row_ptr, s_range);
     const int v0 = s_range[0], v1 = s_range[1];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -331,23 +365,17 @@ conv_fwd_tc_kernel(const ConvDesc D, const float* __restrict__ W1, const __nv_bf
     // B-fragment slots that no path writes (m3 beyond the path, padding slots) stay zero
     for (int i = t; i < D.nBF; i += CONV_THREADS) smem[L.bf + i] = 0.0f;
     for (int i = t; i < D.n_basis * H; i += CONV_THREADS) smem[L.W1 + i] = W1[i];
-    // the x row of a sender in 16-byte pieces, irreps in order: lane j's pieces
-    // j, j + 32, ... (at most TC_XPIECES) with their source and staged offsets
-    int xsrc[TC_XPIECES], xdst[TC_XPIECES], xstr[TC_XPIECES];
+    // bytes of the x rows of one edge (each irrep's block is copied to its own region)
+    unsigned row_bytes = 0;
 #pragma unroll
-    for (int i = 0; i < TC_XPIECES; ++i) {
-        int j = lane + 32 * i, l = 0;
-        while (l < NL - 1 && j >= (2 * l + 1) * D.mul_in[l] / 4) { j -= (2 * l + 1) * D.mul_in[l] / 4; ++l; }
-        const bool ok = j < (2 * l + 1) * D.mul_in[l] / 4;
-        xsrc[i] = ok ? D.x_off[l] + 4 * j : -1;
-        xdst[i] = L.xs + D.xs_off[l] + 4 * j;
-        xstr[i] = D.xs_stride[l];
-    }
+    for (int l = 0; l < NL; ++l) row_bytes += (unsigned)((2 * l + 1) * D.mul_in[l]) * 4u;
+    unsigned parity = 0;
     EdgePrefetch pf;
     pf.fetch(E0, E1, dst, src, geom, row_ptr);
     for (int c0 = E0; c0 < E1; c0 += EC) {
         const int ne = min(EC, E1 - c0);
         __syncthreads();
+        if (t == 0) mbar_expect_tx(&s_bar, row_bytes * (unsigned)ne);   // this chunk's x-row bytes
         if (t < EC) {
             if (t < ne) {
                 s_src[t] = pf.src;
@@ -363,14 +391,16 @@ conv_fwd_tc_kernel(const ConvDesc D, const float* __restrict__ W1, const __nv_bf
             }
         }
         __syncthreads();
-        // x rows of the chunk's senders into shared memory, in flight during the MLP
-        for (int e = warp; e < ne; e += CONV_WARPS) {
-            const float* xr = x + (size_t)s_src[e] * D.x_dim;
-#pragma unroll
-            for (int i = 0; i < TC_XPIECES; ++i)
-                if (xsrc[i] >= 0) cp_async16(smem + xdst[i] + e * xstr[i], xr + xsrc[i]);
+        // x rows of the chunk's senders into shared memory by bulk copies (one per
+        // edge and irrep), in flight during the MLP; the previous chunk's reads of
+        // these regions ended at the barrier above
+        if (lane < NL && D.mul_in[lane]) {           // lane l of warp w copies irrep l of edges w, w + 8
+            const int l = lane;
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            for (int e = warp; e < ne; e += CONV_WARPS)
+                bulk_copy(smem + L.xs + D.xs_off[l] + e * D.xs_stride[l], x + (size_t)s_src[e] * D.x_dim + D.x_off[l],
+                          (unsigned)((2 * l + 1) * D.mul_in[l]) * 4u, &s_bar);
         }
-        cp_async_commit();
         // radial MLP input layer: H1 = silu(B @ W1), thread (j, edge group)
         {
             constexpr int EPT = EC * H / CONV_THREADS;
@@ -407,8 +437,17 @@ conv_fwd_tc_kernel(const ConvDesc D, const float* __restrict__ W1, const __nv_bf
         pf.fetch(c0 + EC, E1, dst, src, geom, row_ptr);
         __syncthreads();
         tc_w_gemm<H>(D, L, smem, W3T_h);
-        cp_async_wait_all();
-        __syncthreads();
+        // the x rows have landed (bounded wait: a copy that never completes is
+        // reported in flags[FLAG_COPY_TIMEOUT] and the CTA's messages are left NaN)
+        const bool ok = mbar_wait(&s_bar, parity, TC_WAIT_LIMIT);
+        parity ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (t == 0 && flags) atomicOr(flags + FLAG_COPY_TIMEOUT, 1);
+            mbar_wait(&s_bar, parity ^ 1u, TC_WAIT_LIMIT);          // once more for the copies in flight
+            for (int v = v0 + warp; v < v1; v += CONV_WARPS)
+                for (int i = lane; i < D.m_dim; i += 32) m[(size_t)v * D.m_dim + i] = __int_as_float(0x7fc00000);
+            return;
+        }
         // receiver boundaries of the chunk: bit e set where a receiver's run starts
         const unsigned segs = __ballot_sync(0xffffffffu, lane < ne && (lane == 0 || s_dst[lane] != s_dst[lane - 1]));
         switch (D.kind) {
@@ -436,11 +475,11 @@ sevennet_status conv_configure_fwd_tc(int H, size_t need) {
 
 void launch_conv_fwd_tc(const LayerDev& Ld, int H, int64_t n_atoms, int64_t n_edges, const int* row_ptr,
                         const int* dst, const int* src, const float4* geom, const float* x, float* m,
-                        cudaStream_t st) {
+                        int* flags, cudaStream_t st) {
     const int grid = conv_grid(n_atoms, 2);
     const size_t sm = conv_tc_smem_bytes(Ld.conv, H);
 #define SN_LT(HH, LL) conv_fwd_tc_kernel<HH, LL><<<grid, CONV_THREADS, sm, st>>>(                     \
-        Ld.conv, Ld.mlp0, Ld.mlp2h, Ld.mlp1Th, (int)n_atoms, (int)n_edges, row_ptr, dst, src, geom, x, m)
+        Ld.conv, Ld.mlp0, Ld.mlp2h, Ld.mlp1Th, (int)n_atoms, (int)n_edges, row_ptr, dst, src, geom, x, m, flags)
     if (H == 64) { if (Ld.conv.lmax == 2) SN_LT(64, 2); else SN_LT(64, 1); }
     else { if (Ld.conv.lmax == 2) SN_LT(32, 2); else SN_LT(32, 1); }
 #undef SN_LT

@@ -413,10 +413,12 @@ sevennet_status run_model(sevennet_model* M, Workspace* ws, const BatchHost& b, 
 // Device status words of a workspace: [0] edge count of the last build or
 // refresh, [1] two atoms closer than 1e-8 A, [2] reverse edge missing, [3]
 // species out of range, [FLAG_GX_OVERFLOW], [FLAG_EDGE_OVERFLOW] edges beyond
-// the capacity, [FLAG_EDGE_NEED] the largest edge count asked for, [7] spare.
+// the capacity, [FLAG_EDGE_NEED] the largest edge count asked for,
+// [FLAG_COPY_TIMEOUT] a bulk copy not completed within its bounded wait.
 constexpr int FLAG_WORDS = 8;
 constexpr int FLAG_EDGE_OVERFLOW = 4;
 constexpr int FLAG_EDGE_NEED = 6;
+constexpr int FLAG_COPY_TIMEOUT = 7;     // a bounded wait for a bulk copy ran out
 
 // Deterministic scatter of dE/dx in the convolution adjoint: every per-edge
 // contribution v is added as the 64-bit integer round(v * 2^36) (fixed point),
@@ -429,9 +431,10 @@ constexpr long long GX_SENTINEL = 1LL << 57;
 constexpr int FLAG_GX_OVERFLOW = 5;
 
 // kernels launchers (conv.cu / node.cu)
+// flags (may be null) receives FLAG_COPY_TIMEOUT from the tensor-core forward
 void launch_conv_fwd(const LayerDev& L, int H, sevennet_precision prec, int64_t n_atoms,
                      int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
-                     const float4* geom, const float* x, float* m, cudaStream_t st);
+                     const float4* geom, const float* x, float* m, cudaStream_t st, int* flags = nullptr);
 // gxq is an [n_atoms][x_dim] 64-bit scratch for the fixed-point sums of dE/dx;
 // gx == nullptr skips their conversion (the first block's input gradient is not
 // needed; the kernel still adds into gxq, which is then left as it is) and flags
@@ -446,7 +449,7 @@ size_t conv_tc_smem_bytes(const ConvDesc& D, int H);
 sevennet_status conv_configure_fwd_tc(int H, size_t need);
 void launch_conv_fwd_tc(const LayerDev& L, int H, int64_t n_atoms, int64_t n_edges, const int* row_ptr,
                         const int* dst, const int* src, const float4* geom, const float* x, float* m,
-                        cudaStream_t st);
+                        int* flags, cudaStream_t st);
 void launch_gemm(const GemmBatch& b, sevennet_precision prec, cudaStream_t st);
 void launch_embed(const float* table, const int* species, int64_t n, int mul0, int n_species, float* h,
                   cudaStream_t st);
