@@ -181,10 +181,14 @@ sevennet_status sevennet_eval_energy_forces_virial(sevennet_model* model, int64_
  * Host arrays: atom_offsets [n_structs+1], cells [n_structs][3][3],
  * pbc [n_structs][3] (NULL = all periodic).  Device arrays: species [N],
  * pos [N][3]; outputs energy [n_structs], forces [N][3], virial
- * [n_structs][3][3].  Returns after enqueueing and one short synchronisation
- * that reads the edge count back (the neighbour-list size decides buffer
- * sizes).  Each structure's results do not depend on the other structures in
- * the batch beyond FP32 rounding. */
+ * [n_structs][3][3].  The neighbour build keeps its edge count on the device
+ * (edge arrays preallocated at 64 per atom or the largest count seen); the
+ * call synchronises once, at its end, to read the status words, and reruns
+ * once with more room if the device reported more edges than the capacity.
+ * Results are bit-for-bit repeatable; in FP32 a structure's results are the
+ * same bits alone and in any batch, in BF16 they agree to BF16 rounding (the
+ * tensor-core forward groups a receiver's edges from chunk boundaries that
+ * move with the batch). */
 sevennet_status sevennet_eval_batch_dev(sevennet_model* model, int32_t n_structs,
                                         const int64_t* atom_offsets, const double* cells,
                                         const int32_t* pbc, const int32_t* species_dev,
@@ -200,9 +204,15 @@ sevennet_status sevennet_eval_batch_dev(sevennet_model* model, int32_t n_structs
  *     [l][m][channel] blocks; m_out [n_atoms][m_dim] FP32 messages, paths
  *     concatenated per l3 in path order.
  * Backward (the adjoint, Eqs. 5 and 8): given g_m, writes g_x (overwritten) and adds dE/dd into g_d
- * (accumulated; zero it first).  prec selects the radial-MLP arithmetic.
- * Both are ordered on `stream` (NULL = the CUDA default stream) and return
- * without synchronising. */
+ * (accumulated; zero it first).  prec selects the arithmetic: FP32 throughout,
+ * or BF16 operands with FP32 accumulation for the radial-MLP products and, in
+ * the forward, the tensor-product contraction (on tensor cores; x must then be
+ * 16-byte aligned, otherwise the FP32-lane contraction runs).  g_x is summed
+ * over edges as 64-bit fixed point (order-independent, so the result is
+ * repeatable bit for bit); a contribution of magnitude >= 2^16 makes its g_x
+ * entry NaN.  Both are ordered on `stream` (NULL = the CUDA default stream)
+ * and return without synchronising; their scratch comes from cudaMallocAsync
+ * on that stream. */
 sevennet_status sevennet_conv_forward_dev(sevennet_model* model, int32_t layer,
                                           int64_t n_atoms, int64_t n_edges,
                                           const int32_t* row_ptr, const int32_t* src,
