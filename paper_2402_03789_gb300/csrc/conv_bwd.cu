@@ -59,7 +59,7 @@ __device__ __forceinline__ void tp_bwd_block(const ConvDesc& D, int u0, int e, i
     constexpr int N1 = 2 * L1 + 1;
     const int mul = D.mul_in[L1];
     const float* xr = x + (size_t)sidx * D.x_dim + D.x_off[L1] + u0;
-    unsigned long long* gxr = gxo + (size_t)sidx * D.x_dim + D.x_off[L1] + u0;
+    unsigned long long* gxr = gxo ? gxo + (size_t)sidx * D.x_dim + D.x_off[L1] + u0 : nullptr;
     float xv[CPL][N1], gx[CPL][N1];
 #pragma unroll
     for (int k = 0; k < CPL; ++k)
@@ -73,10 +73,12 @@ __device__ __forceinline__ void tp_bwd_block(const ConvDesc& D, int u0, int e, i
         tp_bwd_path<L1, BP::list.l2[i], BP::list.l3[i], CPL>(D.paths[BP::begin + i], u0, e, v, xv, gx, gY,
                                                              s_w, D.Wpad, s_G, D.nG, gm, D.m_dim);
     });
+    if (gxr) {                                   // null: the block's dE/dx is not needed
 #pragma unroll
-    for (int k = 0; k < CPL; ++k)
+        for (int k = 0; k < CPL; ++k)
 #pragma unroll
-        for (int a = 0; a < N1; ++a) gx_fixed_add(gxr + a * mul + 32 * k, gx[k][a]);
+            for (int a = 0; a < N1; ++a) gx_fixed_add(gxr + a * mul + 32 * k, gx[k][a]);
+    }
 }
 
 template <int L1, int LMAX, int KIND, int MAXC>
@@ -339,7 +341,8 @@ void launch_conv_bwd(const LayerDev& L, int H, sevennet_precision prec, int64_t 
                      unsigned long long* gxq, int* flags, float* gd, cudaStream_t st) {
     const int lm = L.conv.lmax;
     const size_t nx = (size_t)std::max<int64_t>(n_atoms, 0) * L.conv.x_dim;
-    if (gx && nx) cudaMemsetAsync(gxq, 0, nx * sizeof(unsigned long long), st);
+    if (!gx) gxq = nullptr;                      // the kernel then skips the dE/dx sums
+    if (gxq && nx) cudaMemsetAsync(gxq, 0, nx * sizeof(unsigned long long), st);
     const int grid = conv_grid(n_atoms, conv_ctas_per_sm(lm));
     const size_t sm = smem_bytes(L.conv, H, true, prec == SEVENNET_BF16);
     const bool bf = prec == SEVENNET_BF16;
@@ -354,7 +357,7 @@ void launch_conv_bwd(const LayerDev& L, int H, sevennet_precision prec, int64_t 
         else    { if (lm == 2) SN_LB(32, false, 2); else SN_LB(32, false, 1); }
     }
 #undef SN_LB
-    if (gx && nx)
+    if (gxq && nx)
         gx_from_fixed_kernel<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>((int64_t)nx, gxq, gx, flags);
 }
 
