@@ -636,7 +636,7 @@ sevennet_status model_layer_backward_rest(sevennet_model* M, Workspace* ws, int 
     run_gemm(M, g, prec, st);
     prof_begin(&M->prof, PF_CONV_BWD, st, &ev);
     // the first block's dE/dx is not needed (its input is the species embedding)
-    launch_conv_bwd(L, M->H, prec, N, E, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m,
+    launch_conv_bwd(L, M->H, prec, N, E < 0 ? ws->cap_edges : E, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m,
                     t == 0 ? nullptr : ws->gx, ws->gxq, ws->flags, ws->gd, st);
     prof_end(&M->prof, PF_CONV_BWD, st, ev, t == 0 ? 1 : 2);
     count_launches(t == 0 ? 1 : 2);

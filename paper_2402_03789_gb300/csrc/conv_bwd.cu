@@ -140,31 +140,60 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
                 const __nv_bfloat16* __restrict__ W3T_h, const __nv_bfloat16* __restrict__ W3_h,
                 const __nv_bfloat16* __restrict__ W2T_h, const __nv_bfloat16* __restrict__ W2_h,
                 int n_atoms,
-                int n_edges, const int* __restrict__ row_ptr, const int* __restrict__ dst,
+                int tile_edges, const int* __restrict__ row_ptr, const int* __restrict__ dst,
                 const int* __restrict__ src, const float4* __restrict__ geom,
                 const float* __restrict__ x, const float* __restrict__ gm,
                 unsigned long long* __restrict__ gx, float* __restrict__ gd) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
     const ConvSmem L = conv_smem_layout(D.Wpad, D.WpadB, H, D.nG, D.ys, true, BF);
+    // One tile of tile_edges edges per CTA, CTA k taking tile k: every output is
+    // per edge (dE/dd) or an order-independent sum (dE/dx), so tiles need not
+    // follow receiver boundaries.  CTAs start in index order as earlier ones
+    // finish, so the resident CTAs sweep one narrow window of receivers at a
+    // time, and the senders of that window (atoms near it in the cell-list
+    // order), their x rows and dE/dx sums, stay in L2.
     __shared__ int s_range[2];
-    cta_range(n_atoms, n_edges, row_ptr, s_range);
-    const int v0 = s_range[0], v1 = s_range[1];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int E0 = row_ptr[v0], E1 = row_ptr[v1];
+    if (threadIdx.x == 0) {
+        const long long n_e = row_ptr[n_atoms], lo = (long long)blockIdx.x * tile_edges;
+        s_range[0] = (int)min(lo, n_e);
+        s_range[1] = (int)min(lo + tile_edges, n_e);
+    }
+    __syncthreads();
+    const int E0 = s_range[0], E1 = s_range[1];
+    if (E0 >= E1) return;                        // beyond the device-side edge count
+    const int t = threadIdx.x, warp = t >> 5;
     const int* s_src = reinterpret_cast<const int*>(smem + L.src);
     const int* s_dst = reinterpret_cast<const int*>(smem + L.dst);
     float* s_w = smem + L.w;
     float* s_gY = smem + L.gY;
     load_W1<H>(D, L, smem, W1);
     float* s_gdp = smem + L.gdp;
-    EdgePrefetch pf;
-    pf.fetch(E0, E1, dst, src, geom, row_ptr);
+    // The next chunk's edge records are copied to shared memory asynchronously
+    // (thread e < EC copies edge e), so no registers hold them across a chunk.
+    __shared__ float4 s_ngeo[EC];
+    __shared__ int s_nsrc[EC], s_ndst[EC];
+    auto stage = [&](int c) {
+        if (t < EC && c + t < E1) {
+            cp_async4(reinterpret_cast<float*>(s_nsrc + t), reinterpret_cast<const float*>(src + c + t));
+            cp_async4(reinterpret_cast<float*>(s_ndst + t), reinterpret_cast<const float*>(dst + c + t));
+            cp_async16(s_ngeo + t, geom + c + t);
+        }
+    };
+    stage(E0);
+    cp_async_commit();
+    cp_async_wait_all();
     for (int c0 = E0; c0 < E1; c0 += EC) {
         const int ne = min(EC, E1 - c0);
         __syncthreads();
-        chunk_prologue<H, BF, LMAX>(D, L, smem, c0, ne, pf, W2, W2T_h);
-        pf.fetch(c0 + EC, E1, dst, src, geom, row_ptr);   // next chunk's edges, in flight meanwhile
+        EdgePrefetch cur;
+        if (t < ne) {
+            cur.src = s_nsrc[t];
+            cur.dst = s_ndst[t];
+            cur.geom = s_ngeo[t];
+        }
+        chunk_prologue<H, BF, LMAX>(D, L, smem, c0, ne, cur, W2, W2T_h);
+        stage(c0 + EC);        // lands by the wait before phase G
         // dE/dd of the blocks done so far, copied to shared memory for phase G
         if (t < 3 * ne) cp_async4(s_gdp + t, gd + (size_t)c0 * 3 + t);
         cp_async_commit();
@@ -343,12 +372,17 @@ void launch_conv_bwd(const LayerDev& L, int H, sevennet_precision prec, int64_t 
     const size_t nx = (size_t)std::max<int64_t>(n_atoms, 0) * L.conv.x_dim;
     if (!gx) gxq = nullptr;                      // the kernel then skips the dE/dx sums
     if (gxq && nx) cudaMemsetAsync(gxq, 0, nx * sizeof(unsigned long long), st);
-    const int grid = conv_grid(n_atoms, conv_ctas_per_sm(lm));
+    // tiles of 1..4 chunks, at least about 8 waves of tiles where the input allows
+    // (4 measured fastest on the 24,000-atom cell: 2 and 8 were slower)
+    const int64_t bound = std::max<int64_t>(n_edges, 0);
+    const int64_t wave = (int64_t)conv_grid(INT64_MAX, conv_ctas_per_sm(lm));
+    const int tile = EC * (int)std::min<int64_t>(4, std::max<int64_t>(1, bound / (EC * 8 * wave)));
+    const int grid = (int)std::max<int64_t>(1, (bound + tile - 1) / tile);
     const size_t sm = smem_bytes(L.conv, H, true, prec == SEVENNET_BF16);
     const bool bf = prec == SEVENNET_BF16;
 #define SN_LB(HH, BB, LL) conv_bwd_kernel<HH, BB, LL><<<grid, CONV_THREADS, sm, st>>>(                 \
         L.conv, L.mlp0, L.mlp1, L.mlp1T, L.mlp2, L.mlp2T, L.mlp2h, L.mlp2Th, L.mlp1Th, L.mlp1h,       \
-        (int)n_atoms, (int)n_edges, row_ptr, dst, src, geom, x, gm, gxq, gd)
+        (int)n_atoms, tile, row_ptr, dst, src, geom, x, gm, gxq, gd)
     if (H == 64) {
         if (bf) { if (lm == 3) SN_LB(64, true, 3); else if (lm == 2) SN_LB(64, true, 2); else SN_LB(64, true, 1); }
         else    { if (lm == 3) SN_LB(64, false, 3); else if (lm == 2) SN_LB(64, false, 2); else SN_LB(64, false, 1); }

@@ -9,11 +9,12 @@
 //   w_e = MLP(Bessel(r_e) * envelope(r_e))  (the 1/avg_num_neigh factor is folded into
 //   the last MLP weight matrix on the host).
 // Adjoint (Eqs. 5-8): given g_m = dE/dm, each edge produces dE/dx_src (scattered
-// to the sender with vector-free FP32 reductions), dE/dw_e -> back through the
+// to the sender as 64-bit fixed-point sums), dE/dw_e -> back through the
 // MLP to dE/dr_e, and dE/dY_e; together dE/dd_e, accumulated over blocks.
 //
-// One CTA owns a contiguous range of receivers (balanced by edge count) and
-// walks its edges, sorted by receiver, in chunks of EC edges.  Per chunk:
+// Forward: one CTA owns a contiguous range of receivers (balanced by edge
+// count) and walks its edges, sorted by receiver, in chunks of EC edges.
+// Adjoint: one CTA per tile of up to 4 chunks, tiles in edge order.  Per chunk:
 //   A  geometry: r, unit vector, Y (l <= 2), Bessel basis x envelope  (FP32)
 //   B  radial MLP hidden layers                                      (FFMA)
 //   C  G matrices of every path for every edge of the chunk
@@ -191,6 +192,10 @@ __device__ __forceinline__ void path_G(int kind, const float* Y, float* g) {
 __device__ __forceinline__ void cp_async4(float* s, const float* g) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float4* s, const float4* g) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }

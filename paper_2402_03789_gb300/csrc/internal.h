@@ -435,9 +435,10 @@ constexpr int FLAG_GX_OVERFLOW = 5;
 void launch_conv_fwd(const LayerDev& L, int H, sevennet_precision prec, int64_t n_atoms,
                      int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
                      const float4* geom, const float* x, float* m, cudaStream_t st, int* flags = nullptr);
-// gxq is an [n_atoms][x_dim] 64-bit scratch for the fixed-point sums of dE/dx;
-// gx == nullptr skips them (the first block's input gradient is not needed) and
-// flags (may be null) receives the overflow flag.
+// n_edges is an upper bound on the edge count (the count itself is read from
+// row_ptr[n_atoms] on the device); gxq is an [n_atoms][x_dim] 64-bit scratch for
+// the fixed-point sums of dE/dx; gx == nullptr skips them (the first block's
+// input gradient is not needed) and flags (may be null) receives the overflow flag.
 void launch_conv_bwd(const LayerDev& L, int H, sevennet_precision prec, int64_t n_atoms,
                      int64_t n_edges, const int* row_ptr, const int* dst, const int* src,
                      const float4* geom, const float* x, const float* gm, float* gx,
