@@ -60,7 +60,10 @@ def block_paths(spec, t):
 def conv_flops_per_edge(spec, t, adjoint, tensor_core):
     """Algorithmic FLOPs of the fused convolution kernel per edge for block t,
     split into (FFMA work, tensor-core work).  With tensor_core, the MLP matrix
-    products with H-wide inputs (H x H and H x W) run on tensor cores."""
+    products with H-wide inputs (H x H and H x W) run on tensor cores.  The
+    adjoint of an evaluation runs over unordered pairs of edges: the radial MLP
+    (recompute and input gradient) and the G matrices once per pair, the tensor
+    product once per direction, so per edge the former count half."""
     H, NB = spec.mlp_hidden, spec.n_basis
     paths = block_paths(spec, t)
     W = sum(p[3] for p in paths)
@@ -73,9 +76,9 @@ def conv_flops_per_edge(spec, t, adjoint, tensor_core):
         return mlp_alu + g + tp, mlp_tc
     tp = sum(2 * mu * ((2 * l1 + 1) * (2 * l3 + 1) + 2 * (2 * l1 + 1) + CG_NNZ[(l1, l2, l3)])
              for l1, l2, l3, mu in paths)
-    # forward recompute + input gradient of the MLP
-    mlp_alu, mlp_tc = (2 * first, 2 * mm) if tensor_core else (2 * (first + mm), 0)
-    return mlp_alu + g + tp, mlp_tc
+    # forward recompute + input gradient of the MLP, and the G matrices, once per pair
+    mlp_alu, mlp_tc = (first, mm) if tensor_core else (first + mm, 0)
+    return mlp_alu + g // 2 + tp, mlp_tc
 
 
 def fp32_alu_peak_tflops(n_sm, clock_mhz):

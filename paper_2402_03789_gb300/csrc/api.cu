@@ -42,6 +42,7 @@ int num_sms(int device) {
 // ---------------------------------------------------------------- convolution set-up
 sevennet_status conv_configure_fwd(int H, size_t need);
 sevennet_status conv_configure_bwd(int H, size_t need);
+sevennet_status conv_configure_bwd_pair(int H, size_t need);
 size_t conv_smem_bytes(const ConvDesc& D, int H, bool bwd);
 
 sevennet_status conv_configure(int H, const std::vector<LayerDev>& layers) {
@@ -53,6 +54,7 @@ sevennet_status conv_configure(int H, const std::vector<LayerDev>& layers) {
     }
     SN_TRY(conv_configure_fwd(H, need_f));
     SN_TRY(conv_configure_bwd(H, need_b));
+    SN_TRY(conv_configure_bwd_pair(H, need_b));
     if (need_tc) SN_TRY(conv_configure_fwd_tc(H, need_tc));
     return SEVENNET_OK;
 }
@@ -495,6 +497,7 @@ sevennet_status ws_reserve(sevennet_model* M, Workspace* ws, int64_t n_atoms, in
         SN_TRY(ws_alloc(ws, &ws->species_s, N));
         SN_TRY(ws_alloc(ws, &ws->row_ptr, N + 1));
         SN_TRY(ws_alloc(ws, &ws->row_cnt, N + 1));
+        SN_TRY(ws_alloc(ws, &ws->pair_ptr, N + 1));
         SN_TRY(ws_alloc(ws, &ws->h, N * M->h_max));
         SN_TRY(ws_alloc(ws, &ws->xs, (int64_t)T * N * M->x_max));
         SN_TRY(ws_alloc(ws, &ws->ys, (int64_t)T * N * M->y_max));
@@ -516,6 +519,10 @@ sevennet_status ws_reserve(sevennet_model* M, Workspace* ws, int64_t n_atoms, in
         SN_TRY(ws_alloc(ws, &ws->shift, E * 3));
         SN_TRY(ws_alloc(ws, &ws->rev, E));
         SN_TRY(ws_alloc(ws, &ws->geom, E));
+        SN_TRY(ws_alloc(ws, &ws->p_e, E));
+        SN_TRY(ws_alloc(ws, &ws->p_dst, E));
+        SN_TRY(ws_alloc(ws, &ws->p_src, E));
+        SN_TRY(ws_alloc(ws, &ws->p_geom, E));
         SN_TRY(ws_alloc(ws, &ws->gd, E * 3));
         ws->cap_edges = E;
     }
@@ -623,7 +630,7 @@ void model_layer_backward_gate(sevennet_model* M, Workspace* ws, int t, int64_t 
 // The rest of the adjoint of block t: gm = Lin2^T(gy); conv adjoint (gx, and
 // dE/dd accumulated into gd); for t > 0 gh = Lin1^T(gx) + LinSC^T(gy).
 sevennet_status model_layer_backward_rest(sevennet_model* M, Workspace* ws, int t, int64_t N, int64_t E,
-                                          sevennet_precision prec, cudaStream_t st) {
+                                          sevennet_precision prec, cudaStream_t st, bool pairs) {
     const LayerDev& L = M->layers[t];
     cudaEvent_t ev;
     float* x = ws->xs + (size_t)t * N * M->x_max;
@@ -636,8 +643,13 @@ sevennet_status model_layer_backward_rest(sevennet_model* M, Workspace* ws, int 
     run_gemm(M, g, prec, st);
     prof_begin(&M->prof, PF_CONV_BWD, st, &ev);
     // the first block's dE/dx is not needed (its input is the species embedding)
-    launch_conv_bwd(L, M->H, prec, N, E < 0 ? ws->cap_edges : E, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m,
-                    t == 0 ? nullptr : ws->gx, ws->gxq, ws->flags, ws->gd, st);
+    const int64_t bound = E < 0 ? ws->cap_edges : E;
+    if (pairs)
+        launch_conv_bwd_pair(L, M->H, prec, N, bound, ws->pair_ptr, ws->p_dst, ws->p_src, ws->p_geom, ws->p_e, x,
+                             ws->m, t == 0 ? nullptr : ws->gx, ws->gxq, ws->flags, ws->gd, st);
+    else
+        launch_conv_bwd(L, M->H, prec, N, bound, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m,
+                        t == 0 ? nullptr : ws->gx, ws->gxq, ws->flags, ws->gd, st);
     prof_end(&M->prof, PF_CONV_BWD, st, ev, t == 0 ? 1 : 2);
     count_launches(t == 0 ? 1 : 2);
     if (t == 0) return SEVENNET_OK;
@@ -667,9 +679,14 @@ sevennet_status run_model(sevennet_model* M, Workspace* ws, const BatchHost& b, 
     // reverse path (E < 0: the edge count is on the device; clear the capacity)
     const int64_t E_clear = E < 0 ? ws->cap_edges : E;
     if (E_clear > 0) SN_CUDA(cudaMemsetAsync(ws->gd, 0, (size_t)E_clear * 3 * sizeof(float), st));
+    // the adjoint runs over unordered pairs of the (symmetric) neighbour list
+    prof_begin(&M->prof, PF_NEIGHBORS, st, &ev);
+    build_pairs(ws, N, st);
+    prof_end(&M->prof, PF_NEIGHBORS, st, ev, 3);
+    count_launches(3);
     for (int t = T - 1; t >= 0; --t) {
         model_layer_backward_gate(M, ws, t, N, st);
-        SN_TRY(model_layer_backward_rest(M, ws, t, N, E, prec, st));
+        SN_TRY(model_layer_backward_rest(M, ws, t, N, E, prec, st, true));
     }
     prof_begin(&M->prof, PF_OTHER, st, &ev);
     launch_forces(N, ws->row_ptr, ws->rev, ws->gd, ws->geom, ws->f_s, ws->w_atom, st);

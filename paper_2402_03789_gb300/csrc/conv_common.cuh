@@ -238,6 +238,12 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// The four floats of two packed BF16 pairs (a = (x, y), b = (z, w)).
+__device__ __forceinline__ float4 unpack_bf16x4(uint32_t a, uint32_t b) {
+    return make_float4(__uint_as_float(a << 16), __uint_as_float(a & 0xffff0000u), __uint_as_float(b << 16),
+                       __uint_as_float(b & 0xffff0000u));
+}
+
 // Activations enter the tensor cores as one BF16 value (round to nearest).  W3
 // is one BF16 value too; the hidden-layer weights W2 are a hi + lo BF16 pair
 // (two MMAs), which keeps the virial error of the BF16 path near that of its
@@ -324,7 +330,9 @@ __device__ __forceinline__ void chunk_w_gemm_bf16(const ConvDesc& D, const ConvS
 // reading it (the BF16 adjoint's tile holds at least three [H][EC] partials),
 // and the partials are added in group order, so the result does not depend on
 // the warps' timing.
-template <int H>
+// SPLIT: dE/dw enters as a hi + lo BF16 pair (two MMAs per n tile), which keeps
+// about 16 bits of it (the pair kernel's dE/dw is the sum of two directions).
+template <int H, bool SPLIT = false>
 __device__ __forceinline__ void chunk_gw_gemm_bf16(const ConvDesc& D, const ConvSmem& L, float* smem,
                                                    const __nv_bfloat16* __restrict__ W3h) {
     constexpr int G = 4, WPG = CONV_WARPS / G;
@@ -353,11 +361,20 @@ __device__ __forceinline__ void chunk_gw_gemm_bf16(const ConvDesc& D, const Conv
             const float4 r1 = *reinterpret_cast<const float4*>(s_w + (g + 8) * D.Wpad + c0);
             const uint32_t a[4] = {pack_bf16(r0.x, r0.y), pack_bf16(r1.x, r1.y), pack_bf16(r0.z, r0.w),
                                    pack_bf16(r1.z, r1.w)};
+            uint32_t al[4];
+            if constexpr (SPLIT) {                 // the remainders x - bf16(x)
+                const float4 h0 = unpack_bf16x4(a[0], a[2]), h1 = unpack_bf16x4(a[1], a[3]);
+                al[0] = pack_bf16(r0.x - h0.x, r0.y - h0.y);
+                al[1] = pack_bf16(r1.x - h1.x, r1.y - h1.y);
+                al[2] = pack_bf16(r0.z - h0.z, r0.w - h0.w);
+                al[3] = pack_bf16(r1.z - h1.z, r1.w - h1.w);
+            }
 #pragma unroll
             for (int j = 0; j < NTW; ++j) {
                 const uint32_t* bw = reinterpret_cast<const uint32_t*>(&bv[j]);
                 const uint32_t b[2] = {bw[2 * ks], bw[2 * ks + 1]};
                 mma_bf16(c[j], a, b);
+                if constexpr (SPLIT) mma_bf16(c[j], al, b);
             }
         }
     }
@@ -399,7 +416,8 @@ __device__ __forceinline__ void hidden_load(const __nv_bfloat16* __restrict__ Bn
     }
 }
 
-template <int H>
+// SPLIT: the input also enters as a hi + lo BF16 pair (in_lo * W2_hi added).
+template <int H, bool SPLIT = false>
 __device__ __forceinline__ void hidden_mma(const float* __restrict__ s_in, const HiddenB<H>& bf, float (&c)[4]) {
     constexpr int KSN = H / 16;
     const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
@@ -417,6 +435,14 @@ __device__ __forceinline__ void hidden_mma(const float* __restrict__ s_in, const
         const uint32_t b2[2] = {wl[2 * ks], wl[2 * ks + 1]};
         mma_bf16(c, a, b);
         mma_bf16(c, a, b2);
+        if constexpr (SPLIT) {
+            const float4 h0 = unpack_bf16x4(a[0], a[2]), h1 = unpack_bf16x4(a[1], a[3]);
+            const uint32_t al[4] = {pack_bf16(s_in[hk<H>(k0, g)] - h0.x, s_in[hk<H>(k0 + 1, g)] - h0.y),
+                                    pack_bf16(s_in[hk<H>(k0, g + 8)] - h1.x, s_in[hk<H>(k0 + 1, g + 8)] - h1.y),
+                                    pack_bf16(s_in[hk<H>(k1, g)] - h0.z, s_in[hk<H>(k1 + 1, g)] - h0.w),
+                                    pack_bf16(s_in[hk<H>(k1, g + 8)] - h1.z, s_in[hk<H>(k1 + 1, g + 8)] - h1.w)};
+            mma_bf16(c, al, b);
+        }
     }
 }
 

@@ -338,6 +338,12 @@ struct Workspace {
     int* shift = nullptr;         // [E][3]
     int* rev = nullptr;           // [E]
     float4* geom = nullptr;       // [E] (d, r)
+    // unordered pairs {e, rev[e]} with e < rev[e], in receiver order (the adjoint's units)
+    int* pair_ptr = nullptr;      // [N+1] pairs of receivers < v; pair_ptr[N] = number of pairs
+    int* p_e = nullptr;           // [E] edge of each pair
+    int* p_dst = nullptr;         // [E] its receiver
+    int* p_src = nullptr;         // [E] its sender
+    float4* p_geom = nullptr;     // [E] its (d, r)
     // per-structure descriptors (device)
     double* cells = nullptr;      // [S][9]
     double* inv_cells = nullptr;  // [S][9]
@@ -402,8 +408,10 @@ void model_layer_forward(sevennet_model* M, Workspace* ws, int t, int64_t N, int
                          sevennet_precision prec, cudaStream_t st);
 void model_readout(sevennet_model* M, Workspace* ws, int64_t N, cudaStream_t st);
 void model_layer_backward_gate(sevennet_model* M, Workspace* ws, int t, int64_t N, cudaStream_t st);
+// pairs: the convolution adjoint runs over ws's pair list (built by build_pairs
+// from a symmetric neighbour list); otherwise per edge.
 sevennet_status model_layer_backward_rest(sevennet_model* M, Workspace* ws, int t, int64_t N, int64_t E,
-                                          sevennet_precision prec, cudaStream_t st);
+                                          sevennet_precision prec, cudaStream_t st, bool pairs = false);
 
 // Model evaluation on the internal order prepared by build_neighbors.
 sevennet_status run_model(sevennet_model* M, Workspace* ws, const BatchHost& b, int64_t n_edges,
@@ -451,6 +459,16 @@ void launch_conv_fwd_tc(const LayerDev& L, int H, int64_t n_atoms, int64_t n_edg
                         const int* dst, const int* src, const float4* geom, const float* x, float* m,
                         int* flags, cudaStream_t st);
 void launch_gemm(const GemmBatch& b, sevennet_precision prec, cudaStream_t st);
+// The adjoint over unordered pairs (ws->pair_ptr / p_*): n_pairs is an upper
+// bound on the pair count (the count is pair_ptr[n_atoms], on the device); the
+// pair's whole dE/dd goes to its edge p_e, the reverse edge's entry is left as is.
+void launch_conv_bwd_pair(const LayerDev& L, int H, sevennet_precision prec, int64_t n_atoms, int64_t n_pairs,
+                          const int* pair_ptr, const int* p_dst, const int* p_src, const float4* p_geom,
+                          const int* p_e, const float* x, const float* gm, float* gx, unsigned long long* gxq,
+                          int* flags, float* gd, cudaStream_t st);
+void launch_gx_from_fixed(size_t nx, const unsigned long long* gxq, float* gx, int* flags, cudaStream_t st);
+// The pair list of the current neighbour list (needs row_ptr, rev, dst, src, geom).
+void build_pairs(Workspace* ws, int64_t N, cudaStream_t st);
 void launch_embed(const float* table, const int* species, int64_t n, int mul0, int n_species, float* h,
                   cudaStream_t st);
 void launch_gate_fwd(const LayerDev& L, int mul0, const int* mul, int lmax, int64_t n,

@@ -549,7 +549,8 @@ static double srv_now(const sevennet_server* s) {
 static size_t bytes_per_atom(const sevennet_model* M) {
     const size_t act = (size_t)(M->T * (M->x_max + M->y_max) + M->m_max + M->y_max + M->x_max + 2 * M->h_max) *
                            sizeof(float) + (size_t)M->x_max * sizeof(unsigned long long) + 200;
-    const size_t per_edge = 4 * 4 + 12 + 16 + 12;
+    // dst, src, rev, the clamp's row entries, shift, geometry, dE/dd; the pair list (edge, dst, src, geometry)
+    const size_t per_edge = 4 * 4 + 12 + 16 + 12 + 3 * 4 + 16;
     return act + per_edge * 64;
 }
 

@@ -322,6 +322,48 @@ __global__ void reverse_kernel(int64_t n, int64_t cap, const int* __restrict__ r
     rev[e] = found;
 }
 
+// Unordered pairs: edge e stands for the pair {e, rev[e]} when e < rev[e]
+// (rev[e] != e for every edge of a symmetric list, since d != 0).  A warp per
+// receiver v counts (FILL = false) or writes (FILL = true) its pairs in edge
+// order, so the pair list is ordered by receiver like the edges.
+template <bool FILL>
+__global__ void pairs_kernel(int64_t n, const int* __restrict__ row_ptr, const int* __restrict__ rev,
+                             const int* __restrict__ dst, const int* __restrict__ src,
+                             const float4* __restrict__ geom, int* __restrict__ cnt,
+                             const int* __restrict__ pair_ptr, int* __restrict__ p_e, int* __restrict__ p_dst,
+                             int* __restrict__ p_src, float4* __restrict__ p_geom) {
+    const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (v >= n) return;                                    // whole warps
+    const int e0 = row_ptr[v], e1 = row_ptr[v + 1];
+    int k = FILL ? pair_ptr[v] : 0;
+    for (int b = e0; b < e1; b += 32) {
+        const int e = b + lane;
+        const bool take = e < e1 && e < rev[e];
+        const unsigned m = __ballot_sync(0xffffffffu, take);
+        if (FILL && take) {
+            const int o = k + __popc(m & ((1u << lane) - 1u));
+            p_e[o] = e;
+            p_dst[o] = dst[e];
+            p_src[o] = src[e];
+            p_geom[o] = geom[e];
+        }
+        k += __popc(m);
+    }
+    if (!FILL && lane == 0) cnt[v] = k;
+}
+
+void build_pairs(Workspace* ws, int64_t N, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((std::max<int64_t>(N, 1) * 32 + 255) / 256);
+    if (N > 0)
+        pairs_kernel<false><<<blocks, 256, 0, st>>>(N, ws->row_ptr, ws->rev, nullptr, nullptr, nullptr, ws->row_cnt,
+                                                   nullptr, nullptr, nullptr, nullptr, nullptr);
+    scan_kernel<<<1, 1024, 0, st>>>(ws->row_cnt, N, ws->pair_ptr, nullptr, nullptr);
+    if (N > 0)
+        pairs_kernel<true><<<blocks, 256, 0, st>>>(N, ws->row_ptr, ws->rev, ws->dst, ws->src, ws->geom, nullptr,
+                                                  ws->pair_ptr, ws->p_e, ws->p_dst, ws->p_src, ws->p_geom);
+}
+
 // ---------------------------------------------------------------- host side
 static void cell_geometry(const double* c, double* inv, double* width, double* det_out) {
     const double det = c[0] * (c[4] * c[8] - c[5] * c[7]) - c[1] * (c[3] * c[8] - c[5] * c[6]) +

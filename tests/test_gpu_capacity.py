@@ -43,8 +43,8 @@ def test_server_reruns_a_batch_beyond_its_slot_capacity():
     s = _dense()
     model = sn.SevenNet(spec, w)
     E, F, W = model.evaluate(s.pos, s.cell, s.species, "fp32")
-    # a slot of 64 atoms (about 49 KB each for this model): its 4,096 edges are fewer than the cell needs
-    srv = sn.Server(model, hbm_budget_bytes=3_160_000, n_streams=1, max_batch_structs=4, precision="fp32")
+    # a slot of 64 atoms (about 51 KB each for this model): its 4,096 edges are fewer than the cell needs
+    srv = sn.Server(model, hbm_budget_bytes=3_300_000, n_streams=1, max_batch_structs=4, precision="fp32")
     t = srv.submit(s.pos, s.cell, s.species)
     r, t0 = None, time.time()
     while r is None and time.time() - t0 < 60:
