@@ -644,9 +644,11 @@ sevennet_status model_layer_backward_rest(sevennet_model* M, Workspace* ws, int 
     prof_begin(&M->prof, PF_CONV_BWD, st, &ev);
     // the first block's dE/dx is not needed (its input is the species embedding)
     const int64_t bound = E < 0 ? ws->cap_edges : E;
+    // a symmetric list has exactly E/2 pairs (a list that is not symmetric is an error the
+    // reverse-edge build reports; the grid then covers the first of its pairs only)
     if (pairs)
-        launch_conv_bwd_pair(L, M->H, prec, N, bound, ws->pair_ptr, ws->p_dst, ws->p_src, ws->p_geom, ws->p_e, x,
-                             ws->m, t == 0 ? nullptr : ws->gx, ws->gxq, ws->flags, ws->gd, st);
+        launch_conv_bwd_pair(L, M->H, prec, N, (bound + 1) / 2, ws->pair_ptr, ws->p_dst, ws->p_src, ws->p_geom,
+                             ws->p_e, x, ws->m, t == 0 ? nullptr : ws->gx, ws->gxq, ws->flags, ws->gd, st);
     else
         launch_conv_bwd(L, M->H, prec, N, bound, ws->row_ptr, ws->dst, ws->src, ws->geom, x, ws->m,
                         t == 0 ? nullptr : ws->gx, ws->gxq, ws->flags, ws->gd, st);
