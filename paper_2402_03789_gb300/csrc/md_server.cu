@@ -193,6 +193,7 @@ static sevennet_status md_reserve(sevennet_md* md, int64_t need) {
         cudaFree(md->l_shift);
         md->l_src = md->l_shift = nullptr;
         md->l_cap = 0;
+        md->have_list = false;                     // the stored list is gone: the next step builds one
         if (cudaMalloc(&md->l_src, cap * sizeof(int)) || cudaMalloc(&md->l_shift, cap * 3 * sizeof(int))) {
             cudaGetLastError();
             set_error("cudaMalloc failed for the Verlet list");

@@ -130,6 +130,33 @@ def test_skin_matches_rebuild_every_step():
     b.close()
 
 
+def test_skin_across_calls_matches_rebuild_every_step():
+    # each md_step call sizes the edge capacity from the last count and grows it
+    # when the count rose, which reallocates the stored Verlet list: the next step
+    # must then build a new list rather than filter the old arrays
+    import paper_2402_03789_gb300 as sn
+    s, spec = make_workload("sio2_192_l2")
+    model = get_model(spec)
+    m = s.masses()
+    v = maxwell_boltzmann(m, 3000.0, seed=5)
+    a = sn.MD(model, s.pos, v, s.species, MASSES, s.cell, "fp32")
+    b = sn.MD(model, s.pos, v, s.species, MASSES, s.cell, "fp32")
+    b.set_skin(0.5)
+    a.step(40, 1.0)
+    counts = [b.stats()[1]]
+    for _ in range(8):
+        b.step(5, 1.0)
+        counts.append(b.stats()[1])
+    # a count above all earlier ones before the last call: the next call grew the capacity
+    assert any(counts[k] > max(counts[:k]) for k in range(1, 8)), counts
+    pa, va, fa = a.state()
+    pb, vb, fb = b.state()
+    assert np.abs(pa - pb).max() < 1e-8
+    assert np.abs(fa - fb).max() < 1e-5 * np.sqrt((fa ** 2).mean()) + 1e-9
+    a.close()
+    b.close()
+
+
 def test_skin_rejects_negative():
     import paper_2402_03789_gb300 as sn
     s, spec = make_workload("sio2_192_l2")
