@@ -1018,7 +1018,7 @@ sevennet_status check_flags(const int* f) {
     SN_CHECK(f[FLAG_GX_OVERFLOW] == 0, SEVENNET_EOVERFLOW,
              "a feature gradient in the convolution adjoint reached 2^16 (outside the fixed-point range)");
     SN_CHECK(f[FLAG_EDGE_OVERFLOW] == 0, SEVENNET_EOVERFLOW, "neighbour list larger than its capacity");
-    SN_CHECK(f[2] == 0, SEVENNET_ECUDA, "internal error: reverse edge not found");
+    SN_CHECK(f[2] == 0, SEVENNET_ECUDA, "internal error: inconsistent neighbour list (a reverse edge not found, or a stored Verlet list entry out of range)");
     SN_CHECK(f[FLAG_COPY_TIMEOUT] == 0, SEVENNET_ETIMEDOUT, "a bulk copy did not complete within its bounded wait");
     return SEVENNET_OK;
 }

@@ -395,10 +395,12 @@ sevennet_status build_neighbors(sevennet_model* M, Workspace* ws, const BatchHos
 // made it: row_ptr, src, shift) that are within the model's r_c at the current
 // positions (input order), kept in list order, into ws->row_ptr/src/dst/shift/
 // geom/rev.  One structure; the internal order and cell of that build stay valid.
-// Asynchronous (*n_edges_out = -1; the count stays on the device).
+// Asynchronous (*n_edges_out = -1; the count stays on the device).  list_cap is
+// the number of entries the list arrays hold: a row beyond it or a sender that
+// is not an atom is skipped and sets flags[2].
 sevennet_status refresh_neighbors(sevennet_model* M, Workspace* ws, int64_t n_atoms, const double* pos_dev,
                                   const int* list_row_ptr, const int* list_src, const int* list_shift,
-                                  cudaStream_t st, int64_t* n_edges_out);
+                                  int64_t list_cap, cudaStream_t st, int64_t* n_edges_out);
 
 // The steps of run_model, for callers that interleave work between blocks
 // (the domain-decomposed evaluation): all operate on the N atoms and E edges of

@@ -232,7 +232,7 @@ static sevennet_status md_evaluate(sevennet_md* md) {
         N, std::max<int64_t>(md->l_cap, 3 * N + 1), md->cond, md->ws->row_ptr, md->ws->src, md->ws->shift, md->pos,
         md->l_row, md->l_src, md->l_shift, md->ref);
     md->have_list = true;
-    SN_TRY(refresh_neighbors(M, md->ws, N, md->pos, md->l_row, md->l_src, md->l_shift, md->st, &E));
+    SN_TRY(refresh_neighbors(M, md->ws, N, md->pos, md->l_row, md->l_src, md->l_shift, md->l_cap, md->st, &E));
     return run_model(M, md->ws, md->b, -1, md->prec, md->ev, md->f, md->ev + 1, md->st);
 }
 

@@ -490,7 +490,8 @@ __global__ void __launch_bounds__(128)
 refresh_kernel(int64_t n, double rc2, int64_t cap, const int* __restrict__ perm, const double* __restrict__ pos,
                const double* __restrict__ cell, const int* __restrict__ lrow, const int* __restrict__ lsrc,
                const int* __restrict__ lshift, const int* __restrict__ row_ptr, int* __restrict__ counts,
-               int* __restrict__ dst, int* __restrict__ src, int* __restrict__ shift, float4* __restrict__ geom) {
+               int* __restrict__ dst, int* __restrict__ src, int* __restrict__ shift, float4* __restrict__ geom,
+               int* __restrict__ flags, int64_t lcap) {
     const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / NGL;
     if (v >= n) return;
     const int j = threadIdx.x & (NGL - 1);
@@ -499,14 +500,22 @@ refresh_kernel(int64_t n, double rc2, int64_t cap, const int* __restrict__ perm,
     const int64_t ov = perm[v];
     const double pv[3] = {pos[ov * 3], pos[ov * 3 + 1], pos[ov * 3 + 2]};
     int64_t e = FILL ? (int64_t)row_ptr[v] : 0;
-    const int k1 = lrow[v + 1];
-    for (int k0 = lrow[v]; k0 < k1; k0 += NGL) {
+    int k1 = lrow[v + 1];
+    const int kb = lrow[v];
+    if (kb < 0 || (int64_t)k1 > lcap || kb > k1) {       // rows outside the stored list: reported
+        if (!FILL && j == 0) atomicOr(flags + 2, 1);
+        k1 = kb;
+    }
+    for (int k0 = kb; k0 < k1; k0 += NGL) {
         const int k = k0 + j;
         bool hit = false;
         double dd[3], r2 = 0.0;
         int w = 0, s0 = 0, s1 = 0, s2 = 0;
-        if (k < k1) {
-            w = lsrc[k];
+        if (k < k1) w = lsrc[k];
+        if (k < k1 && (w < 0 || (int64_t)w >= n)) {     // not an atom: a corrupt list, reported
+            if (!FILL) atomicOr(flags + 2, 1);
+            w = 0;
+        } else if (k < k1) {
             s0 = lshift[k * 3]; s1 = lshift[k * 3 + 1]; s2 = lshift[k * 3 + 2];
             const int64_t ow = perm[w];
 #pragma unroll
@@ -538,18 +547,18 @@ refresh_kernel(int64_t n, double rc2, int64_t cap, const int* __restrict__ perm,
 
 sevennet_status refresh_neighbors(sevennet_model* M, Workspace* ws, int64_t N, const double* pos_dev,
                                   const int* list_row_ptr, const int* list_src, const int* list_shift,
-                                  cudaStream_t st, int64_t* n_edges_out) {
+                                  int64_t list_cap, cudaStream_t st, int64_t* n_edges_out) {
     // asynchronous: the count stays on the device, the arrays are sized by capacity
     const double rc = M->cfg.r_cut;
     if (N > 0)
         refresh_kernel<false><<<blocks_for(N * NGL, 128), 128, 0, st>>>(
             N, rc * rc, 0, ws->perm, pos_dev, ws->cells, list_row_ptr, list_src, list_shift, nullptr,
-            ws->row_cnt, nullptr, nullptr, nullptr, nullptr);
+            ws->row_cnt, nullptr, nullptr, nullptr, nullptr, ws->flags, list_cap);
     scan_kernel<<<1, 1024, 0, st>>>(ws->row_cnt, N, ws->row_ptr, ws->flags + 0, nullptr);
     if (N > 0) {
         refresh_kernel<true><<<blocks_for(N * NGL, 128), 128, 0, st>>>(
             N, rc * rc, ws->cap_edges, ws->perm, pos_dev, ws->cells, list_row_ptr, list_src, list_shift,
-            ws->row_ptr, nullptr, ws->dst, ws->src, ws->shift, ws->geom);
+            ws->row_ptr, nullptr, ws->dst, ws->src, ws->shift, ws->geom, ws->flags, list_cap);
         clamp_rows_kernel<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, ws->row_ptr, ws->cap_edges, ws->flags,
                                                                  nullptr);
     }
