@@ -14,7 +14,10 @@
 //              exchange of partial forces, Figure 3f); the virial sums
 //              -dE/dd (x) d over all edges of all domains.
 // The exchanges go through device buffers indexed by global atom.  The result
-// equals the single-domain evaluation up to FP summation order.
+// equals the single-domain evaluation up to FP summation order, and repeats
+// bit for bit: the sums that several domains or edges add into (ghost
+// gradients, forces) are 64-bit fixed point, and the virial's per-block
+// partials are added in block order.
 #include "internal.h"
 
 #include <algorithm>
@@ -41,28 +44,44 @@ __global__ void dd_get_rows(int64_t n, int w, const int* __restrict__ gid, const
     loc[i] = glob[(int64_t)gid[r] * w + (i % w)];
 }
 
-// glob[gid[i]] += loc[i] (several domains may hold the same ghost)
+// glob[gid[i]] += loc[i] in 64-bit fixed point (units of 2^-36; several domains
+// may hold the same ghost, and integer sums do not depend on the order of the
+// adds); a value that is not finite or has |v| >= 2^16 adds a sentinel instead.
 __global__ void dd_push_grad(int64_t n, int w, const int* __restrict__ gid, const float* __restrict__ loc,
-                             float* __restrict__ glob) {
+                             unsigned long long* __restrict__ glob) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n * w) return;
     const int64_t r = i / w;
-    atomicAdd(glob + (int64_t)gid[r] * w + (i % w), loc[i]);
+    const float v = loc[i];
+    const long long q = fabsf(v) < GX_LIMIT ? __float2ll_rn(v * GX_SCALE) : GX_SENTINEL;
+    atomicAdd(glob + (int64_t)gid[r] * w + (i % w), (unsigned long long)q);
 }
 
-// loc[i] += glob[gid[i]]
-__global__ void dd_pull_grad(int64_t n, int w, const int* __restrict__ gid, const float* __restrict__ glob,
+// loc[i] += glob[gid[i]] (a sum that received the sentinel gives NaN)
+__global__ void dd_pull_grad(int64_t n, int w, const int* __restrict__ gid, const unsigned long long* __restrict__ glob,
                              float* __restrict__ loc) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n * w) return;
     const int64_t r = i / w;
-    loc[i] += glob[(int64_t)gid[r] * w + (i % w)];
+    const long long q = (long long)glob[(int64_t)gid[r] * w + (i % w)];
+    const long long lim = 1LL << 56;
+    loc[i] += (q >= lim || q <= -lim) ? __int_as_float(0x7fc00000) : (float)((double)q * (1.0 / 68719476736.0));
 }
 
-// Edge e (receiver v <- sender w): F[v] += g_e, F[w] -= g_e; W -= g_e (x) d_e.
+// Force contributions in 64-bit fixed point (units of 2^-36 eV/A); a value
+// that is not finite or has |v| >= 2^26 adds a sentinel, which gives NaN.
+constexpr double DD_F_LIMIT = 67108864.0;
+__device__ __forceinline__ void dd_force_add(unsigned long long* p, double v) {
+    const long long q = fabs(v) < DD_F_LIMIT ? __double2ll_rn(v * 68719476736.0) : GX_SENTINEL;
+    atomicAdd(p, (unsigned long long)q);
+}
+
+// Edge e (receiver v <- sender w): F[v] += g_e, F[w] -= g_e (fixed point); the
+// block's sum of -g_e (x) d_e goes to the partials Wp[blockIdx.x][9].
 __global__ void dd_forces(int64_t E, const int* __restrict__ dst, const int* __restrict__ src,
                           const int* __restrict__ gid, const float* __restrict__ gd,
-                          const float4* __restrict__ geom, double* __restrict__ F, double* __restrict__ W) {
+                          const float4* __restrict__ geom, unsigned long long* __restrict__ Fq,
+                          double* __restrict__ Wp) {
     __shared__ double red[9][256];
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double wv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -73,8 +92,8 @@ __global__ void dd_forces(int64_t E, const int* __restrict__ dst, const int* __r
         const int64_t v = gid[dst[e]], w = gid[src[e]];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            atomicAdd(F + v * 3 + a, g[a]);
-            atomicAdd(F + w * 3 + a, -g[a]);
+            dd_force_add(Fq + v * 3 + a, g[a]);
+            dd_force_add(Fq + w * 3 + a, -g[a]);
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -90,7 +109,23 @@ __global__ void dd_forces(int64_t E, const int* __restrict__ dst, const int* __r
             for (int k = 0; k < 9; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x < 9) atomicAdd(W + threadIdx.x, red[threadIdx.x][0]);
+    if (threadIdx.x < 9) Wp[(int64_t)blockIdx.x * 9 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// F from its fixed-point sums; W = the nb block partials added in block order.
+__global__ void dd_forces_out(int64_t n, const unsigned long long* __restrict__ Fq, double* __restrict__ F,
+                              int64_t nb, const double* __restrict__ Wp, double* __restrict__ W) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 3 * n) {
+        const long long q = (long long)Fq[i];
+        const long long lim = 1LL << 56;
+        F[i] = (q >= lim || q <= -lim) ? __longlong_as_double(0x7ff8000000000000LL) : (double)q * (1.0 / 68719476736.0);
+    }
+    if (i < 9) {
+        double s = 0.0;
+        for (int64_t b = 0; b < nb; ++b) s += Wp[b * 9 + i];
+        W[i] = s;
+    }
 }
 
 static inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
@@ -150,7 +185,8 @@ extern "C" sevennet_status sevennet_eval_decomposed(sevennet_model* M, int64_t n
         if (!seen_own[i]) own[dom[i]].push_back((int)i);
     sevennet_status status = SEVENNET_OK;
     float *gbuf = nullptr;
-    double *F = nullptr, *W = nullptr;
+    unsigned long long *gq = nullptr, *Fq = nullptr;
+    double *F = nullptr, *W = nullptr, *Wp = nullptr;
     const cudaStream_t st = M->stream;
     auto cleanup = [&]() {
         for (auto& d : D) {
@@ -158,8 +194,11 @@ extern "C" sevennet_status sevennet_eval_decomposed(sevennet_model* M, int64_t n
             cudaFree(d.gid);
         }
         cudaFree(gbuf);
+        cudaFree(gq);
+        cudaFree(Fq);
         cudaFree(F);
         cudaFree(W);
+        cudaFree(Wp);
     };
     std::vector<int> loc(n_atoms, -1);
     for (int d = 0; d < n_domains && status == SEVENNET_OK; ++d) {
@@ -224,10 +263,15 @@ extern "C" sevennet_status sevennet_eval_decomposed(sevennet_model* M, int64_t n
     const int T = M->T;
     int64_t wmax = 0;
     for (int t = 0; t < T; ++t) wmax = std::max<int64_t>(wmax, std::max(M->layers[t].h_in_dim, M->layers[t].h_out_dim));
+    int64_t n_part = 0;                          // virial partials: one per block of dd_forces
+    for (auto& d : D) n_part += d.E > 0 ? nblk(d.E) : 0;
     if (status == SEVENNET_OK &&
         (cudaMalloc(&gbuf, (size_t)n_atoms * wmax * sizeof(float)) != cudaSuccess ||
+         cudaMalloc(&gq, (size_t)n_atoms * wmax * sizeof(unsigned long long)) != cudaSuccess ||
+         cudaMalloc(&Fq, (size_t)n_atoms * 3 * sizeof(unsigned long long)) != cudaSuccess ||
          cudaMalloc(&F, (size_t)n_atoms * 3 * sizeof(double)) != cudaSuccess ||
-         cudaMalloc(&W, 9 * sizeof(double)) != cudaSuccess)) {
+         cudaMalloc(&W, 9 * sizeof(double)) != cudaSuccess ||
+         cudaMalloc(&Wp, (size_t)std::max<int64_t>(n_part, 1) * 9 * sizeof(double)) != cudaSuccess)) {
         cudaGetLastError();
         set_error("cudaMalloc failed for the exchange buffers");
         status = SEVENNET_ENOMEM;
@@ -252,13 +296,13 @@ extern "C" sevennet_status sevennet_eval_decomposed(sevennet_model* M, int64_t n
     for (int t = T - 1; t >= 0 && status == SEVENNET_OK; --t) {
         const int w = M->layers[t].h_out_dim;
         if (t < T - 1) {      // reverse exchange of dE/dh left on ghosts
-            SN_CUDA(cudaMemsetAsync(gbuf, 0, (size_t)n_atoms * w * sizeof(float), st));
+            SN_CUDA(cudaMemsetAsync(gq, 0, (size_t)n_atoms * w * sizeof(unsigned long long), st));
             for (auto& d : D)
                 if (d.n_loc > d.n_own)
                     dd_push_grad<<<nblk((d.n_loc - d.n_own) * w), 256, 0, st>>>(
-                        d.n_loc - d.n_own, w, d.gid + d.n_own, d.ws->gh + d.n_own * w, gbuf);
+                        d.n_loc - d.n_own, w, d.gid + d.n_own, d.ws->gh + d.n_own * w, gq);
             for (auto& d : D) {
-                if (d.n_own) dd_pull_grad<<<nblk(d.n_own * w), 256, 0, st>>>(d.n_own, w, d.gid, gbuf, d.ws->gh);
+                if (d.n_own) dd_pull_grad<<<nblk(d.n_own * w), 256, 0, st>>>(d.n_own, w, d.gid, gq, d.ws->gh);
                 if (d.n_loc > d.n_own)
                     SN_CUDA(cudaMemsetAsync(d.ws->gh + d.n_own * w, 0, (size_t)(d.n_loc - d.n_own) * w * sizeof(float),
                                             st));
@@ -276,11 +320,15 @@ extern "C" sevennet_status sevennet_eval_decomposed(sevennet_model* M, int64_t n
     }
     if (status) { cleanup(); return status; }
     // forces, virial, energy
-    SN_CUDA(cudaMemsetAsync(F, 0, (size_t)n_atoms * 3 * sizeof(double), st));
-    SN_CUDA(cudaMemsetAsync(W, 0, 9 * sizeof(double), st));
+    SN_CUDA(cudaMemsetAsync(Fq, 0, (size_t)n_atoms * 3 * sizeof(unsigned long long), st));
+    int64_t part = 0;
     for (auto& d : D)
-        if (d.E > 0)
-            dd_forces<<<nblk(d.E), 256, 0, st>>>(d.E, d.ws->dst, d.ws->src, d.gid, d.ws->gd, d.ws->geom, F, W);
+        if (d.E > 0) {
+            dd_forces<<<nblk(d.E), 256, 0, st>>>(d.E, d.ws->dst, d.ws->src, d.gid, d.ws->gd, d.ws->geom, Fq,
+                                                 Wp + part * 9);
+            part += nblk(d.E);
+        }
+    dd_forces_out<<<nblk(std::max<int64_t>(3 * n_atoms, 9)), 256, 0, st>>>(n_atoms, Fq, F, part, Wp, W);
     double e_sum = 0.0;
     std::vector<double> ea;
     for (auto& d : D) {

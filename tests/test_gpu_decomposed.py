@@ -1,7 +1,8 @@
 """Single-process emulation of the spatial decomposition (Sec. 3.1, Figure 3):
 the energy, forces and virial with the cell cut into 2-4 slab domains, each
 exchanging ghost features forward and gradients and partial forces backward
-after every block, equal the single-domain evaluation (and the oracle)."""
+after every block, equal the single-domain evaluation (and the oracle), and
+repeat bit for bit."""
 
 import numpy as np
 import pytest
@@ -59,6 +60,17 @@ def test_decomposed_bf16_within_bf16_bounds_3000():
     e_pa, f_rel, w_rel = errors(E, F, W, E1, F1, W1, s.n_atoms)
     print(f"decomposed bf16 vs fp32: |dE|/N {e_pa:.2e} F {f_rel:.2e} W {w_rel:.2e}")
     assert e_pa < 5e-6 and f_rel < 5e-3 and w_rel < 5e-3, (e_pa, f_rel, w_rel)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_decomposed_repeats_bitwise(prec):
+    # ghost gradients and forces are summed in 64-bit fixed point and the virial's
+    # partials in a fixed order, so two evaluations give the same bits
+    s, spec = make_workload("sio2_192_l2")
+    model = get_model(spec)
+    E1, F1, W1 = model.evaluate_decomposed(s.pos, s.cell, s.species, 3, prec)
+    E2, F2, W2 = model.evaluate_decomposed(s.pos, s.cell, s.species, 3, prec)
+    assert E1 == E2 and np.array_equal(F1, F2) and np.array_equal(W1, W2)
 
 
 def test_decomposed_rejects_bad_domain_count():
