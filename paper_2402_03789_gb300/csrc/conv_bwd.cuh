@@ -297,28 +297,28 @@ conv_bwd_kernel(const ConvDesc D, const float* __restrict__ W1, const float* __r
                 const float* __restrict__ W2T, const float* __restrict__ W3, const float* __restrict__ W3T,
                 const __nv_bfloat16* __restrict__ W3T_h, const __nv_bfloat16* __restrict__ W3_h,
                 const __nv_bfloat16* __restrict__ W2T_h, const __nv_bfloat16* __restrict__ W2_h,
-                int tile_edges, const int* __restrict__ count, const int* __restrict__ dst,
+                int tile_units, const int* __restrict__ count, const int* __restrict__ dst,
                 const int* __restrict__ src, const float4* __restrict__ geom, const int* __restrict__ eidx,
                 const float* __restrict__ x, const float* __restrict__ gm,
                 unsigned long long* __restrict__ gx, float* __restrict__ gd) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
     const ConvSmem L = conv_smem_layout(D.Wpad, D.WpadB, H, D.nG, D.ys, true, BF);
-    // One tile of tile_edges edges per CTA, CTA k taking tile k: every output is
-    // per edge (dE/dd) or an order-independent sum (dE/dx), so tiles need not
-    // follow receiver boundaries.  CTAs start in index order as earlier ones
+    // One tile of tile_units units (edges or pairs) per CTA, CTA k taking tile k:
+    // every output is per unit (dE/dd) or an order-independent sum (dE/dx), so
+    // tiles need not follow receiver boundaries.  CTAs start in index order as earlier ones
     // finish, so the resident CTAs sweep one narrow window of receivers at a
     // time, and the senders of that window (atoms near it in the cell-list
     // order), their x rows and dE/dx sums, stay in L2.
     __shared__ int s_range[2];
     if (threadIdx.x == 0) {
-        const long long n_e = *count, lo = (long long)blockIdx.x * tile_edges;
+        const long long n_e = *count, lo = (long long)blockIdx.x * tile_units;
         s_range[0] = (int)min(lo, n_e);
-        s_range[1] = (int)min(lo + tile_edges, n_e);
+        s_range[1] = (int)min(lo + tile_units, n_e);
     }
     __syncthreads();
     const int E0 = s_range[0], E1 = s_range[1];
-    if (E0 >= E1) return;                        // beyond the device-side edge count
+    if (E0 >= E1) return;                        // beyond the device-side unit count
     const int t = threadIdx.x, warp = t >> 5;
     const int* s_src = reinterpret_cast<const int*>(smem + L.src);
     const int* s_dst = reinterpret_cast<const int*>(smem + L.dst);
