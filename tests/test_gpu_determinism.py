@@ -7,7 +7,7 @@ the result of a structure is also bit-identical alone and inside a batch: each
 receiver's messages are summed edge by edge in list order whatever the chunk
 boundaries.  In BF16 the tensor-core forward groups a receiver's edges into MMA
 K groups that start at chunk boundaries, and those move with the batch, so the
-two agree to the BF16 path's rounding only (bounded below).
+two agree to FP32 rounding carried through the BF16 operands (bounded below at 1e-5).
 """
 
 import numpy as np
@@ -63,4 +63,5 @@ def test_bf16_alone_and_in_batch_agree():
         E1, F1, W1 = model.evaluate(s.pos, s.cell, s.species, "bf16")
         e_pa, f_rel, w_rel = errors(e[i], f[off[i]:off[i + 1]], w[i], E1, F1, W1, s.n_atoms)
         print(f"bf16 structure {i}: |dE|/N {e_pa:.2e} F {f_rel:.2e} W {w_rel:.2e}")
-        assert e_pa <= 1e-6 and f_rel <= 1e-3 and w_rel <= 1e-3
+        # measured at most 7.3e-7 (forces) and 3.5e-7 (virial) on these structures
+        assert e_pa <= 1e-8 and f_rel <= 1e-5 and w_rel <= 1e-5
